@@ -1,0 +1,221 @@
+/*
+ * ifci.h — C ABI of the GB300 (sm_103a) library for the iFCI increment CI solve.
+ *
+ * Method (arXiv 2307.10675, Methods, "Incremental Full Configuration
+ * Interaction", Eqs. 1-5): the correlation energy is expanded over bodies
+ * (localized occupied orbitals), E_c = sum_i eps_i + sum_{i>j} eps_ij + ...,
+ * with eps_X = E_c(X) - sum of the increments of every non-empty proper
+ * subset of X.  E_c(X) = E_X - E_0 where E_X is the lowest singlet CI energy
+ * with only the orbitals of body set X correlated (the other bodies' bonding
+ * orbitals frozen doubly occupied, their virtuals removed) and E_0 is the
+ * energy of the single reference determinant (Methods, last paragraph).
+ * The paper solves each E_X with HBCI; this library solves it exactly
+ * (determinant FCI + Davidson), whose cost is the sigma build sigma = H c.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an int status (ifci_status_t below).  On failure
+ *   ifci_last_error_string(handle) describes the most recent error.
+ * - "device" pointers are CUDA global memory on the handle's device, owned
+ *   by the caller; the library never frees them.  "host" pointers are plain
+ *   CPU memory.  Scratch memory comes only from the handle's workspace.
+ * - Asynchronous calls are ordered on the cudaStream_t argument (0 = legacy
+ *   default stream).  Calls documented as synchronous return after their
+ *   results are written.
+ * - Orbital pair index: pair(p,q) = P(P+1)/2 + Q with P = max(p,q),
+ *   Q = min(p,q); npair = n(n+1)/2.  Packed two-electron integrals are the
+ *   symmetric npair x npair row-major matrix V[pair(pq)][pair(rs)] = (pq|rs)
+ *   (chemist notation, real orbitals).
+ * - Strings: the nstr = C(norb, nelec_spin) occupation bit masks of one
+ *   spin, ordered by increasing integer value (bit p = orbital p).  A CI
+ *   vector is the row-major nstr x nstr matrix c[I_alpha][I_beta] of the
+ *   determinants |I_alpha I_beta> = A+(I_alpha) B+(I_beta)|0>.
+ * - Limits: norb <= 31 (pair index fits 9 bits), nstr < 2^22.
+ */
+#ifndef IFCI_H
+#define IFCI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *ifci_stream_t; /* same object as cudaStream_t */
+
+typedef enum {
+    IFCI_OK = 0,
+    IFCI_ERR_INVALID_ARG = 1,   /* bad size, pointer or option; nothing was launched */
+    IFCI_ERR_OOM = 2,           /* workspace could not grow */
+    IFCI_ERR_CUDA = 3,          /* a CUDA runtime call failed (message has the CUDA error) */
+    IFCI_ERR_NOT_CONVERGED = 4, /* at least one problem hit max_iter; per-problem status says which */
+    IFCI_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out */
+    IFCI_ERR_UNSUPPORTED = 6    /* precision or size this build does not provide */
+} ifci_status_t;
+
+typedef enum {
+    IFCI_FP64 = 0, /* every step in FP64 */
+    IFCI_FP32 = 1, /* sigma contraction with FP32 inputs, FP32 accumulation */
+    IFCI_TF32 = 2, /* sigma contraction on tensor cores, TF32 inputs, FP32 accumulation */
+    IFCI_BF16 = 3  /* sigma contraction on tensor cores, BF16 inputs, FP32 accumulation */
+} ifci_precision_t;
+
+typedef struct ifci_handle_s *ifci_handle_t;
+
+/* ---------------------------------------------------------------- handle */
+
+/* Creates a handle bound to CUDA device `device` with `workspace_bytes` of
+ * scratch reserved up front (0 = none).  Calls grow the workspace when they
+ * need more.  Not thread-safe: one host thread per handle at a time. */
+int ifci_handle_create(ifci_handle_t *handle, size_t workspace_bytes, int device);
+int ifci_handle_destroy(ifci_handle_t handle);
+/* Message of the most recent failed call on this handle ("" if none).  The
+ * string stays valid until the next call on the handle. */
+const char *ifci_last_error_string(ifci_handle_t handle);
+/* Bytes of workspace currently held by the handle. */
+size_t ifci_workspace_bytes(ifci_handle_t handle);
+/* Number of kernel launches this handle has issued since creation. */
+long long ifci_kernel_launches(ifci_handle_t handle);
+
+/* ---------------------------------------------------------------- strings */
+
+/* Host-only.  nstr = C(norb, nelec_spin); nexc = excitations per string =
+ * nelec_spin * (norb - nelec_spin + 1) (one per occupied orbital for the
+ * diagonal E_pp, one per occupied/empty orbital pair). */
+int ifci_string_counts(int norb, int nelec_spin, int *nstr, int *nexc);
+
+/* ifci_build_strings — occupation strings and single-excitation table
+ * (the alpha/beta string layer of the determinant CI that solves E_X).
+ *   strings : device uint64[nstr], output, ascending bit masks.
+ *   exc     : device int32[nstr * nexc], output.  Row I lists, in ascending
+ *             pair order, every nonzero E_pq |I> = s |J> with p,q such that
+ *             p == q (q occupied) or exactly one of p,q occupied; entry =
+ *             (J << 10) | (pair(p,q) << 1) | (s < 0).
+ * Asynchronous on `stream`.  Errors: INVALID_ARG for sizes out of range. */
+int ifci_build_strings(ifci_handle_t handle, int norb, int nelec_spin,
+                       uint64_t *strings, int32_t *exc, ifci_stream_t stream);
+
+typedef struct {
+    int norb, nelec_spin, nstr, nexc;
+    const uint64_t *strings;  /* device, from ifci_build_strings */
+    const int32_t *exc;       /* device, from ifci_build_strings */
+} ifci_strings_t;
+
+/* ---------------------------------------------------------------- Hamiltonian pieces */
+
+/* ifci_sigma — sigma = H c for one CI space (the per-increment hot loop).
+ *   H = sum_pq h1_pq E_pq + 1/2 sum_pqrs (pq|rs) (E_pq E_rs - delta_qr E_ps)
+ * with E_pq the spin-summed excitation operators, no constant term.
+ *   h1    : device double[norb*norb], symmetric one-electron integrals.
+ *   eri   : device double[npair*npair], packed (pq|rs).
+ *   c     : device double[nstr*nstr], input vector.
+ *   sigma : device double[nstr*nstr], output (must not alias c).
+ *   precision : ifci_precision_t of the contraction (FP64 exact path;
+ *               the others round the contraction inputs, FP32 accumulate).
+ * Asynchronous on `stream`; uses handle workspace (grows it if needed). */
+int ifci_sigma(ifci_handle_t handle, const ifci_strings_t *str,
+               const double *h1, const double *eri, const double *c, double *sigma,
+               int precision, ifci_stream_t stream);
+
+/* ifci_hdiag — diagonal <I|H|I> of the same H (no constant), for the
+ * Davidson preconditioner.  hd: device double[nstr*nstr].  Asynchronous. */
+int ifci_hdiag(ifci_handle_t handle, const ifci_strings_t *str,
+               const double *h1, const double *eri, double *hd, ifci_stream_t stream);
+
+/* ---------------------------------------------------------------- systems */
+
+typedef struct {
+    int nbody;               /* number of bodies N */
+    const int *body_offset;  /* host int[nbody+1]; body b owns orbitals
+                                [off[b], off[b+1]); its first orbital is its
+                                bonding (reference-occupied) orbital */
+    int norb;                /* total orbitals = off[nbody] */
+    const double *h;         /* double[norb*norb] one-electron integrals */
+    const double *eri;       /* double[npair*npair] packed (pq|rs) */
+    int on_host;             /* 1: h and eri are host pointers (copied in by
+                                the call), 0: device pointers */
+} ifci_system_t;
+
+/* ifci_frozen_core — the effective CI problem of body set X (Methods,
+ * definition of E_c(X)): core C = bonding orbitals of bodies not in X,
+ * active A = orbitals of the bodies in X (ascending global index).
+ *   E_core = sum_c 2 h_cc + sum_{c,d} [2 (cc|dd) - (cd|dc)]
+ *   h1_pq  = h_pq + sum_c [2 (pq|cc) - (pc|cq)]           (p, q in A)
+ *   eri_x  = (pq|rs) restricted to A, packed over A's local pair index.
+ * bodies: host int[nx], distinct, ascending.  h1: device double[nA*nA];
+ * eri_x: device double[npairA^2]; e_core: host double*.  Synchronous. */
+int ifci_frozen_core(ifci_handle_t handle, const ifci_system_t *sys, int nx, const int *bodies,
+                     double *h1, double *eri_x, double *e_core, ifci_stream_t stream);
+
+/* ---------------------------------------------------------------- Davidson */
+
+typedef struct {
+    int norb, nelec_spin;
+    const double *h1;   /* device double[norb*norb] */
+    const double *eri;  /* device double[npair*npair] packed */
+    double e_core;      /* constant added to the eigenvalue */
+    double *c_out;      /* device double[nstr*nstr] converged vector, or NULL */
+} ifci_problem_t;
+
+typedef struct {
+    int precision;       /* ifci_precision_t of the bulk sigma contraction */
+    int max_iter;        /* Davidson iterations per problem (default 100) */
+    int max_space;       /* subspace size before a restart, 3..24 (default 12) */
+    double e_tol;        /* convergence: |E_k - E_{k-1}| < e_tol (default 1e-10 Eh) */
+    double r_tol;        /* and ||H x - E x||_2 < r_tol (default 1e-6) */
+    int refine;          /* non-FP64 precision: finish with FP64 sigma refinement (default 1) */
+    long long det_budget;/* determinants per sigma wave (0 = from workspace size) */
+} ifci_davidson_opts_t;
+
+/* Fills opts with the defaults listed above (precision IFCI_FP64). */
+void ifci_davidson_default_opts(ifci_davidson_opts_t *opts);
+
+/* ifci_davidson_batched — lowest singlet eigenpair of each problem's
+ * H + e_core (Davidson in the spin-flip-even sector c = c^T, which holds
+ * S = 0, 2, ...; diagonal preconditioner; classical Gram-Schmidt done twice).
+ *   energies : host double[nprob], eigenvalues including e_core.
+ *   iters    : host int[nprob] or NULL, sigma builds per problem.
+ *   status   : host int[nprob] or NULL, IFCI_OK or IFCI_ERR_NOT_CONVERGED.
+ * Synchronous.  Returns NOT_CONVERGED if any problem did not converge. */
+int ifci_davidson_batched(ifci_handle_t handle, int nprob, const ifci_problem_t *probs,
+                          const ifci_davidson_opts_t *opts, double *energies, int *iters,
+                          int *status, ifci_stream_t stream);
+
+/* ---------------------------------------------------------------- increments */
+
+/* Host-only: number of body sets of size 1..max_order (their order, used by
+ * every per-set array: by size, then lexicographic in body index). */
+int ifci_num_subsets(int nbody, int max_order, long long *count);
+
+/* ifci_increments — the iFCI expansion truncated at max_order (Eqs. 1-5).
+ *   e0      : host double*, reference energy E_0.
+ *   e_x     : host double[nsub] or NULL, E_X per body set.
+ *   eps     : host double[nsub], increments eps_X.
+ *   e_total : host double*, E_0 + sum eps_X.
+ *   status  : host int[nsub] or NULL, per-set Davidson status.
+ * Keeps the converged vectors in the handle when opts->refine >= 0 so that
+ * ifci_rdm_backward can reuse them.  Synchronous. */
+int ifci_increments(ifci_handle_t handle, const ifci_system_t *sys, int max_order,
+                    const ifci_davidson_opts_t *opts, double *e0, double *e_x, double *eps,
+                    double *e_total, int *status, ifci_stream_t stream);
+
+/* ifci_rdm_backward — gradient of E_iFCI (truncated at max_order) with
+ * respect to the inputs h and V by Hellmann–Feynman on every E_Y:
+ *   dE/dh_pq    = grad_out * sum_Y w_Y gamma^Y_pq + (1 - sum w) gamma^0_pq
+ *   dE/dV[A][B] = grad_out * 1/2 sum over ordered (p,q) in A, (r,s) in B of
+ *                 [sum_Y w_Y Gamma^Y_pqrs + (1 - sum w) Gamma^0_pqrs]
+ * with w_Y = (-1)^(n-|Y|) C(N-|Y|-1, n-|Y|), gamma/Gamma the spin-summed
+ * full-space 1-/2-RDMs of E_Y's vector.  dh: device double[norb*norb];
+ * deri: device double[npair*npair]; both overwritten.
+ * recompute_vectors = 0 reuses the vectors of the last ifci_increments on
+ * this handle for the same system (INVALID_ARG if there are none).
+ * Synchronous. */
+int ifci_rdm_backward(ifci_handle_t handle, const ifci_system_t *sys, int max_order,
+                      const ifci_davidson_opts_t *opts, double grad_out,
+                      double *dh, double *deri, int recompute_vectors, ifci_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IFCI_H */

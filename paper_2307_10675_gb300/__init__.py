@@ -1,0 +1,12 @@
+"""GB300 (sm_103a) library for the iFCI increment CI solve of arXiv 2307.10675.
+
+The compute path is the CUDA library ``_build/libifci.so`` (C ABI in
+``include/ifci.h``); this package only marshals arguments to it.
+"""
+from .api import (  # noqa: F401
+    IFCI_BF16, IFCI_FP32, IFCI_FP64, IFCI_TF32, PRECISIONS,
+    CIProblem, Handle, IfciError, StringTables, SystemArrays,
+    body_subsets, davidson_opts,
+    ifci_build_strings, ifci_davidson_batched, ifci_frozen_core, ifci_hdiag, ifci_increments,
+    ifci_num_subsets, ifci_rdm_backward, ifci_sigma, ifci_string_counts,
+)

@@ -1,0 +1,91 @@
+// Internal helpers of the iFCI GB300 library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string>
+#include <vector>
+
+#include "../../include/ifci.h"
+
+struct ifci_handle_s {
+    int device = 0;
+    char *ws = nullptr;          // workspace base (device)
+    size_t ws_bytes = 0;         // capacity
+    size_t ws_top = 0;           // bump pointer
+    std::string last_error;
+    long long launches = 0;
+    // vectors kept by ifci_increments for ifci_rdm_backward
+    struct Kept {
+        bool valid = false;
+        int nbody = 0, max_order = 0, norb = 0;
+        std::vector<int> body_offset;
+        const void *h_ptr = nullptr, *eri_ptr = nullptr;
+        double *vec = nullptr;               // device, all vectors back to back
+        size_t vec_bytes = 0;
+        std::vector<long long> vec_off;      // per subset offset (doubles)
+    } kept;
+};
+
+namespace ifci {
+
+constexpr int kPairBits = 9;       // pair index < 512  => norb <= 31
+constexpr int kMaxNorb = 31;
+constexpr int kMaxStr = 1 << 22;
+
+__host__ __device__ inline int pair_of(int p, int q) {
+    int P = p > q ? p : q, Q = p > q ? q : p;
+    return P * (P + 1) / 2 + Q;
+}
+__host__ __device__ inline int exc_J(int32_t e) { return (int)((uint32_t)e >> 10); }
+__host__ __device__ inline int exc_pair(int32_t e) { return (e >> 1) & 511; }
+__host__ __device__ inline double exc_sign(int32_t e) { return (e & 1) ? -1.0 : 1.0; }
+
+long long binom(int n, int k);
+
+// error bookkeeping ------------------------------------------------------
+int set_error(ifci_handle_t h, int code, const char *fmt, ...);
+
+#define IFCI_CUDA_TRY(h, expr)                                                        \
+    do {                                                                              \
+        cudaError_t _e = (expr);                                                      \
+        if (_e != cudaSuccess)                                                        \
+            return ifci::set_error((h), IFCI_ERR_CUDA, "%s:%d %s: %s", __FILE__,      \
+                                   __LINE__, #expr, cudaGetErrorString(_e));          \
+    } while (0)
+
+#define IFCI_LAUNCH_CHECK(h)                                                          \
+    do {                                                                              \
+        (h)->launches++;                                                              \
+        cudaError_t _e = cudaGetLastError();                                          \
+        if (_e != cudaSuccess)                                                        \
+            return ifci::set_error((h), IFCI_ERR_CUDA, "%s:%d launch: %s", __FILE__,  \
+                                   __LINE__, cudaGetErrorString(_e));                 \
+    } while (0)
+
+#define IFCI_TRY(expr)                  \
+    do {                                \
+        int _s = (expr);                \
+        if (_s != IFCI_OK) return _s;   \
+    } while (0)
+
+// workspace --------------------------------------------------------------
+// Calls reserve what they need up front (ws_reserve), then carve pieces with
+// ws_take in the same order.  Growing synchronises the device first.
+int ws_reserve(ifci_handle_t h, size_t bytes);
+void ws_reset(ifci_handle_t h);
+template <typename T>
+T *ws_take(ifci_handle_t h, size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    if (h->ws_top + bytes > h->ws_bytes) return nullptr;
+    T *p = reinterpret_cast<T *>(h->ws + h->ws_top);
+    h->ws_top += bytes;
+    return p;
+}
+inline size_t ws_round(size_t bytes) { return (bytes + 255) & ~size_t(255); }
+
+inline cudaStream_t as_cuda(ifci_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int device_sm_count(int device);
+
+}  // namespace ifci

@@ -1,0 +1,34 @@
+// Host-side Davidson driver shared by ifci_davidson_batched and ifci_increments.
+#pragma once
+#include "davidson.cuh"
+
+namespace ifci {
+
+struct ProbSpec {
+    int n, m;               // active orbitals, electrons per spin
+    const double *h1;       // device n*n
+    const double *eri;      // device npair*npair
+    double e_core;
+    double *c_out;          // device nstr*nstr or nullptr
+};
+
+struct DavSizes {
+    size_t bytes = 0;
+    int nitem = 0, nclass = 0;
+    long long max_pd = 0, sum_pd = 0, budget = 0;
+    long long n_items_sigma = 0, n_tiles_sigma = 0;
+};
+
+int check_opts(ifci_handle_t h, const ifci_davidson_opts_t &o);
+// Upper bound of the workspace dav_solve takes (with ws_take) for these problems.
+size_t dav_workspace_bytes(const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o);
+// Solves every problem; carves its memory from the handle workspace after
+// whatever the caller already took.  Outputs are host arrays (may be null
+// except energies).  Synchronous.
+int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o, double *energies,
+              int *iters, int *status, cudaStream_t s);
+int dav_init(ifci_handle_t h, DavBatch &b, cudaStream_t s);
+int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_plan, int *d_hi, int *d_lo,
+                void *D, void *G, int *h_nactive, cudaStream_t s);
+
+}  // namespace ifci

@@ -1,0 +1,581 @@
+// Batched Davidson for the lowest singlet root of many CI problems at once.
+//
+// Every step is a batched kernel over all problems still iterating; the
+// per-problem state (subspace size, Ritz value, flags) lives on the device, so
+// the host only launches and reads one counter per iteration.  All
+// orthogonalisation, Rayleigh quotients and residuals are FP64.
+//
+// Vector passes of one iteration (k = subspace size):
+//   sigma(b_new) -> subspace column <b_j|sigma_new> -> k x k Jacobi eigen-solve
+//   -> residual r = sum_j y_j (sigma_j - theta b_j), correction t = r / (theta - H_II)
+//   -> classical Gram-Schmidt twice -> normalise, symmetrise (c = c^T sector).
+//
+// Two precisions of sigma (mixed mode): corrections get the low-precision
+// sigma; each restart vector x (the current Ritz vector) gets the FP64 sigma,
+// and convergence is only judged on x, whose Rayleigh quotient and residual
+// are then exact to FP64 rounding.  The low-precision error enters only
+// through the corrections, whose weight shrinks with the residual.
+#include <algorithm>
+#include <cmath>
+
+#include "dav_driver.cuh"
+#include "hamiltonian.cuh"
+
+namespace ifci {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block reduction of NV values per thread into out[0..NV).  256 threads.
+template <int NV>
+__device__ void block_sum_store(double (&v)[NV], int nv, double *out) {
+    __shared__ double red[8][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; j++) {
+        if (j < nv) {
+            double s = warp_sum(v[j]);
+            if (lane == 0) red[warp][j] = s;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        double s = 0.0;
+        for (int w = 0; w < 8; w++) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ setup
+
+// Starting vector: the closed-shell determinant (I, I) of lowest diagonal.
+__global__ void init_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st) {
+    const DavProb p = probs[blockIdx.x];
+    __shared__ double bv[256];
+    __shared__ int bi[256];
+    double best = 1e300;
+    int besti = 0;
+    for (int i = threadIdx.x; i < p.nstr; i += blockDim.x) {
+        double v = p.hd[(long long)i * p.nstr + i];
+        if (v < best) { best = v; besti = i; }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = besti;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            double v2 = bv[threadIdx.x + o];
+            int i2 = bi[threadIdx.x + o];
+            if (v2 < bv[threadIdx.x] || (v2 == bv[threadIdx.x] && i2 < bi[threadIdx.x])) {
+                bv[threadIdx.x] = v2;
+                bi[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        DavState s{};
+        s.k = 1;
+        s.newest = 0;
+        s.active = 1;
+        s.restart = 0;
+        s.iters = 0;
+        s.status = IFCI_ERR_NOT_CONVERGED;
+        s.tslot = -1;
+        s.ref = bi[0] * p.nstr + bi[0];
+        s.theta = bv[0];
+        s.theta_prev = 1e300;
+        s.rnorm = 1e300;
+        s.tnorm2 = 0.0;
+        s.energy = 0.0;
+        st[blockIdx.x] = s;
+    }
+}
+
+__global__ void init_vec_kernel(const DavProb *__restrict__ probs, const DavState *__restrict__ st,
+                                const WorkItem *__restrict__ items) {
+    const WorkItem it = items[blockIdx.x];
+    const DavProb &p = probs[it.prob];
+    const int ref = st[it.prob].ref;
+    long long end = min(it.start + (long long)kVecChunk, p.ndet);
+    for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) p.B[I] = (I == ref) ? 1.0 : 0.0;
+}
+
+// sigma selectors for the mixed mode: hi for the restart vector (k == 1), lo otherwise
+__global__ void select_kernel(const DavState *__restrict__ st, int nprob, int mixed, int *__restrict__ hi,
+                              int *__restrict__ lo) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nprob) return;
+    const DavState s = st[i];
+    int a = s.active;
+    if (mixed) {
+        hi[i] = a && s.k == 1;
+        lo[i] = a && s.k > 1;
+    } else {
+        hi[i] = a;
+        lo[i] = 0;
+    }
+}
+
+// ------------------------------------------------------------------ subspace
+
+// partial[item][j] = <b_j | sigma_new> over the item's determinants, j <= newest
+__global__ void __launch_bounds__(256) dots_kernel(const DavProb *__restrict__ probs, const DavState *__restrict__ st,
+                                                   const WorkItem *__restrict__ items, double *__restrict__ part) {
+    const WorkItem it = items[blockIdx.x];
+    const DavState s = st[it.prob];
+    if (!s.active) return;
+    const DavProb &p = probs[it.prob];
+    const int k = s.newest + 1;
+    double acc[kMaxSpace + 1];
+#pragma unroll
+    for (int j = 0; j <= kMaxSpace; j++) acc[j] = 0.0;
+    const double *Sn = p.S + (long long)s.newest * p.ndet;
+    long long end = min(it.start + (long long)kVecChunk, p.ndet);
+    for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) {
+        double sv = Sn[I];
+#pragma unroll
+        for (int j = 0; j <= kMaxSpace; j++)
+            if (j < k) acc[j] += p.B[(long long)j * p.ndet + I] * sv;
+    }
+    block_sum_store<kMaxSpace + 1>(acc, k, part + (long long)blockIdx.x * kNP);
+}
+
+// Cyclic Jacobi on a symmetric k x k matrix (k <= kMaxSpace): lowest eigenpair.
+__device__ void jacobi_lowest(double *A, double *V, int k, double *theta, double *y) {
+    for (int i = 0; i < k; i++)
+        for (int j = 0; j < k; j++) V[i * kMaxSpace + j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 60; sweep++) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < k; i++)
+            for (int j = 0; j < k; j++) {
+                double a = A[i * kMaxSpace + j];
+                tot += a * a;
+                if (i != j) off += a * a;
+            }
+        if (off <= 1e-30 * tot || off == 0.0) break;
+        for (int pp = 0; pp < k - 1; pp++)
+            for (int q = pp + 1; q < k; q++) {
+                double apq = A[pp * kMaxSpace + q];
+                if (apq == 0.0) continue;
+                double app = A[pp * kMaxSpace + pp], aqq = A[q * kMaxSpace + q];
+                double tau = (aqq - app) / (2.0 * apq);
+                double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+                for (int r = 0; r < k; r++) {
+                    double arp = A[r * kMaxSpace + pp], arq = A[r * kMaxSpace + q];
+                    A[r * kMaxSpace + pp] = c * arp - sn * arq;
+                    A[r * kMaxSpace + q] = sn * arp + c * arq;
+                }
+                for (int r = 0; r < k; r++) {
+                    double apr = A[pp * kMaxSpace + r], aqr = A[q * kMaxSpace + r];
+                    A[pp * kMaxSpace + r] = c * apr - sn * aqr;
+                    A[q * kMaxSpace + r] = sn * apr + c * aqr;
+                }
+                for (int r = 0; r < k; r++) {
+                    double vrp = V[r * kMaxSpace + pp], vrq = V[r * kMaxSpace + q];
+                    V[r * kMaxSpace + pp] = c * vrp - sn * vrq;
+                    V[r * kMaxSpace + q] = sn * vrp + c * vrq;
+                }
+            }
+    }
+    int best = 0;
+    for (int i = 1; i < k; i++)
+        if (A[i * kMaxSpace + i] < A[best * kMaxSpace + best]) best = i;
+    *theta = A[best * kMaxSpace + best];
+    // fix the sign so that the largest component is positive (deterministic)
+    int big = 0;
+    for (int i = 1; i < k; i++)
+        if (fabs(V[i * kMaxSpace + best]) > fabs(V[big * kMaxSpace + best])) big = i;
+    double sg = V[big * kMaxSpace + best] < 0 ? -1.0 : 1.0;
+    for (int i = 0; i < k; i++) y[i] = sg * V[i * kMaxSpace + best];
+}
+
+// One block per problem: finish the subspace column and solve the projected problem.
+__global__ void solve_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st,
+                             const double *__restrict__ part, double *__restrict__ gs, double *__restrict__ ys) {
+    const int i = blockIdx.x;
+    DavState s = st[i];
+    if (!s.active) return;
+    const DavProb p = probs[i];
+    const int k = s.newest + 1;
+    double *Gm = gs + (long long)i * kMaxSpace * kMaxSpace;
+    __shared__ double col[kMaxSpace + 1];
+    if (threadIdx.x < k) {
+        double v = 0.0;
+        for (int w = 0; w < p.nitem; w++) v += part[(long long)(p.item0 + w) * kNP + threadIdx.x];
+        col[threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < k; j++) {
+            Gm[j * kMaxSpace + s.newest] = col[j];
+            Gm[s.newest * kMaxSpace + j] = col[j];
+        }
+        double A[kMaxSpace * kMaxSpace], V[kMaxSpace * kMaxSpace], y[kMaxSpace];
+        for (int a = 0; a < k; a++)
+            for (int b = 0; b < k; b++) A[a * kMaxSpace + b] = 0.5 * (Gm[a * kMaxSpace + b] + Gm[b * kMaxSpace + a]);
+        double theta;
+        jacobi_lowest(A, V, k, &theta, y);
+        for (int j = 0; j < kNP; j++) ys[(long long)i * kNP + j] = j < k ? y[j] : 0.0;
+        s.theta = theta;
+        s.iters += 1;
+        st[i] = s;
+    }
+}
+
+// t = sum_j y_j (S_j - theta B_j); ||t||^2; t /= (theta - H_II); dots <b_j|t>.
+__global__ void __launch_bounds__(256) residual_kernel(const DavProb *__restrict__ probs,
+                                                       const DavState *__restrict__ st,
+                                                       const WorkItem *__restrict__ items,
+                                                       const double *__restrict__ ys, int max_space,
+                                                       double *__restrict__ part) {
+    const WorkItem it = items[blockIdx.x];
+    const DavState s = st[it.prob];
+    if (!s.active) return;
+    const DavProb &p = probs[it.prob];
+    const int k = s.newest + 1;
+    const double theta = s.theta;
+    double y[kMaxSpace];
+#pragma unroll
+    for (int j = 0; j < kMaxSpace; j++) y[j] = ys[(long long)it.prob * kNP + j];
+    double acc[kMaxSpace + 2];
+#pragma unroll
+    for (int j = 0; j < kMaxSpace + 2; j++) acc[j] = 0.0;
+    double *T = p.B + (long long)max_space * p.ndet;   // scratch slot for the correction
+    long long end = min(it.start + (long long)kVecChunk, p.ndet);
+    for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) {
+        double r = 0.0;
+        double bv[kMaxSpace];
+#pragma unroll
+        for (int j = 0; j < kMaxSpace; j++) {
+            if (j < k) {
+                bv[j] = p.B[(long long)j * p.ndet + I];
+                r += y[j] * (p.S[(long long)j * p.ndet + I] - theta * bv[j]);
+            }
+        }
+        acc[kMaxSpace + 1] += r * r;
+        double den = theta - p.hd[I];
+        if (fabs(den) < 1e-4) den = den < 0 ? -1e-4 : 1e-4;
+        double t = r / den;
+        T[I] = t;
+#pragma unroll
+        for (int j = 0; j < kMaxSpace; j++)
+            if (j < k) acc[j] += bv[j] * t;
+        acc[kMaxSpace] += t * t;
+    }
+    // layout of part: [0..k) dots, kMaxSpace: |t|^2, kMaxSpace+1: |r|^2
+    __shared__ double red[8][kMaxSpace + 2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < kMaxSpace + 2; j++) {
+        if (j < k || j >= kMaxSpace) {
+            double v = warp_sum(acc[j]);
+            if (lane == 0) red[warp][j] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kMaxSpace + 2 && (threadIdx.x < k || threadIdx.x >= kMaxSpace)) {
+        double v = 0.0;
+        for (int w = 0; w < 8; w++) v += red[w][threadIdx.x];
+        part[(long long)blockIdx.x * kNP + threadIdx.x] = v;
+    }
+}
+
+// Convergence test, restart decision, CGS coefficients.  One block per problem.
+__global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st,
+                             const double *__restrict__ part, double *__restrict__ coef, const double *__restrict__ ys,
+                             double *__restrict__ gs, int max_space, int restart_at, int mixed, int max_iter,
+                             double e_tol, double r_tol, int *__restrict__ nactive) {
+    const int i = blockIdx.x;
+    DavState s = st[i];
+    if (!s.active) return;
+    const DavProb p = probs[i];
+    const int k = s.newest + 1;
+    __shared__ double sum[kMaxSpace + 2];
+    if (threadIdx.x < kMaxSpace + 2 && (threadIdx.x < k || threadIdx.x >= kMaxSpace)) {
+        double v = 0.0;
+        for (int w = 0; w < p.nitem; w++) v += part[(long long)(p.item0 + w) * kNP + threadIdx.x];
+        sum[threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    s.rnorm = sqrt(sum[kMaxSpace + 1]);
+    const double *y = ys + (long long)i * kNP;
+    bool exact = !mixed || k == 1;
+    bool conv = exact && s.rnorm < r_tol && fabs(s.theta - s.theta_prev) < e_tol;
+    if (exact) s.theta_prev = s.theta;
+    if (conv || s.rnorm == 0.0) {
+        s.active = 0;
+        s.status = IFCI_OK;
+        s.energy = s.theta + p.e_core;
+        s.tslot = -1;
+        st[i] = s;
+        return;
+    }
+    if (s.iters >= max_iter) {
+        s.active = 0;
+        s.status = IFCI_ERR_NOT_CONVERGED;
+        s.energy = s.theta + p.e_core;
+        s.tslot = -1;
+        st[i] = s;
+        return;
+    }
+    atomicAdd(nactive, 1);
+    double *c = coef + (long long)i * kNP;
+    double *Gm = gs + (long long)i * kMaxSpace * kMaxSpace;
+    if (k >= restart_at) {
+        s.restart = 1;
+        if (mixed) {
+            // basis becomes [x]; its FP64 sigma is built next iteration
+            s.k = 1;
+            s.newest = 0;
+            s.tslot = -1;
+        } else {
+            // basis becomes [x, t]; <x|t> = sum_j y_j <b_j|t>
+            double xt = 0.0;
+            for (int j = 0; j < k; j++) xt += y[j] * sum[j];
+            c[0] = xt;
+            for (int j = 1; j < kNP; j++) c[j] = 0.0;
+            s.k = 1;
+            s.tslot = 1;
+            Gm[0] = s.theta;
+        }
+    } else {
+        s.restart = 0;
+        for (int j = 0; j < kNP; j++) c[j] = j < k ? sum[j] : 0.0;
+        s.tslot = k;
+    }
+    s.tnorm2 = sum[kMaxSpace];
+    st[i] = s;
+}
+
+// Restart: B_0 <- sum y_j B_j, S_0 <- sum y_j S_j, slot 1 <- correction (FP64 mode).
+__global__ void __launch_bounds__(256) restart_kernel(const DavProb *__restrict__ probs,
+                                                      const DavState *__restrict__ st,
+                                                      const WorkItem *__restrict__ items, const double *__restrict__ ys,
+                                                      int max_space, int old_k, int mixed) {
+    const WorkItem it = items[blockIdx.x];
+    const DavState s = st[it.prob];
+    if (!s.active || !s.restart) return;
+    const DavProb &p = probs[it.prob];
+    double y[kMaxSpace];
+#pragma unroll
+    for (int j = 0; j < kMaxSpace; j++) y[j] = ys[(long long)it.prob * kNP + j];
+    long long end = min(it.start + (long long)kVecChunk, p.ndet);
+    const double *T = p.B + (long long)max_space * p.ndet;
+    for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) {
+        double x = 0.0, sx = 0.0;
+#pragma unroll
+        for (int j = 0; j < kMaxSpace; j++) {
+            if (j < old_k) {
+                x += y[j] * p.B[(long long)j * p.ndet + I];
+                sx += y[j] * p.S[(long long)j * p.ndet + I];
+            }
+        }
+        p.B[I] = x;
+        p.S[I] = sx;
+        if (!mixed) p.B[p.ndet + I] = T[I];
+    }
+}
+
+// t -= sum_{j<k} coef_j b_j ; then dots <b_j|t> and |t|^2 for the next pass.
+__global__ void __launch_bounds__(256) ortho_kernel(const DavProb *__restrict__ probs, const DavState *__restrict__ st,
+                                                    const WorkItem *__restrict__ items,
+                                                    const double *__restrict__ coef, int max_space,
+                                                    double *__restrict__ part) {
+    const WorkItem it = items[blockIdx.x];
+    const DavState s = st[it.prob];
+    if (!s.active || s.tslot < 0) return;
+    const DavProb &p = probs[it.prob];
+    const int k = s.k;
+    double c[kMaxSpace];
+#pragma unroll
+    for (int j = 0; j < kMaxSpace; j++) c[j] = coef[(long long)it.prob * kNP + j];
+    double *T = p.B + (long long)(s.restart ? 1 : s.tslot) * p.ndet;
+    if (!s.restart && s.tslot == k) T = p.B + (long long)max_space * p.ndet;
+    double acc[kMaxSpace + 1];
+#pragma unroll
+    for (int j = 0; j <= kMaxSpace; j++) acc[j] = 0.0;
+    long long end = min(it.start + (long long)kVecChunk, p.ndet);
+    for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) {
+        double t = T[I];
+        double bv[kMaxSpace];
+#pragma unroll
+        for (int j = 0; j < kMaxSpace; j++)
+            if (j < k) {
+                bv[j] = p.B[(long long)j * p.ndet + I];
+                t -= c[j] * bv[j];
+            }
+        T[I] = t;
+#pragma unroll
+        for (int j = 0; j < kMaxSpace; j++)
+            if (j < k) acc[j] += bv[j] * t;
+        acc[kMaxSpace] += t * t;
+    }
+    __shared__ double red[8][kMaxSpace + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j <= kMaxSpace; j++) {
+        if (j < k || j == kMaxSpace) {
+            double v = warp_sum(acc[j]);
+            if (lane == 0) red[warp][j] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x <= kMaxSpace && (threadIdx.x < k || threadIdx.x == kMaxSpace)) {
+        double v = 0.0;
+        for (int w = 0; w < 8; w++) v += red[w][threadIdx.x];
+        part[(long long)blockIdx.x * kNP + threadIdx.x] = v;
+    }
+}
+
+__global__ void reduce_coef_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st,
+                                   const double *__restrict__ part, double *__restrict__ coef) {
+    const int i = blockIdx.x;
+    DavState s = st[i];
+    if (!s.active || s.tslot < 0) return;
+    const DavProb p = probs[i];
+    const int k = s.k;
+    if (threadIdx.x < k || threadIdx.x == kMaxSpace) {
+        double v = 0.0;
+        for (int w = 0; w < p.nitem; w++) v += part[(long long)(p.item0 + w) * kNP + threadIdx.x];
+        if (threadIdx.x == kMaxSpace) st[i].tnorm2 = v;
+        else coef[(long long)i * kNP + threadIdx.x] = v;
+    }
+    if (threadIdx.x > k && threadIdx.x < kMaxSpace) coef[(long long)i * kNP + threadIdx.x] = 0.0;
+}
+
+// b_k = t / |t|, symmetrised over (I_a, I_b) <-> (I_b, I_a); the new slot becomes
+// the next sigma target.  One thread per pair (I, I^T) with I_a >= I_b.
+__global__ void __launch_bounds__(256) normalize_kernel(const DavProb *__restrict__ probs,
+                                                        const DavState *__restrict__ st,
+                                                        const WorkItem *__restrict__ items, int max_space) {
+    const WorkItem it = items[blockIdx.x];
+    const DavState s = st[it.prob];
+    if (!s.active || s.tslot < 0) return;
+    const DavProb &p = probs[it.prob];
+    const double inv = s.tnorm2 > 0.0 ? 1.0 / sqrt(s.tnorm2) : 0.0;
+    double *T = p.B + (long long)(s.restart ? 1 : s.tslot) * p.ndet;
+    double *dst = T;
+    if (!s.restart && s.tslot == s.k) {
+        T = p.B + (long long)max_space * p.ndet;
+        dst = p.B + (long long)s.k * p.ndet;
+    }
+    long long end = min(it.start + (long long)kVecChunk, p.ndet);
+    const int n = p.nstr;
+    for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) {
+        int a = (int)(I / n), b = (int)(I % n);
+        if (a < b) continue;
+        long long It = (long long)b * n + a;
+        double v = 0.5 * (T[I] + T[It]) * inv;
+        dst[I] = v;
+        dst[It] = v;
+    }
+}
+
+__global__ void advance_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st, int nprob,
+                               double r_tol) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nprob) return;
+    DavState s = st[i];
+    if (!s.active) return;
+    if (s.tslot >= 0 && s.tnorm2 < 1e-28) {
+        // the correction vanished after orthogonalisation: the subspace is exhausted
+        s.active = 0;
+        s.status = s.rnorm < r_tol ? IFCI_OK : IFCI_ERR_NOT_CONVERGED;
+        s.energy = s.theta + probs[i].e_core;
+        st[i] = s;
+        return;
+    }
+    if (s.tslot >= 0) {
+        int slot = s.restart ? 1 : s.tslot;
+        s.newest = slot;
+        s.k = slot + 1;
+    }
+    s.restart = 0;
+    st[i] = s;
+}
+
+// c_out = sum_j y_j B_j for every finished problem that asked for it
+__global__ void __launch_bounds__(256) ritz_out_kernel(const DavProb *__restrict__ probs,
+                                                       const DavState *__restrict__ st,
+                                                       const WorkItem *__restrict__ items,
+                                                       const double *__restrict__ ys) {
+    const WorkItem it = items[blockIdx.x];
+    const DavProb &p = probs[it.prob];
+    if (!p.c_out) return;
+    const DavState s = st[it.prob];
+    const int k = s.newest + 1;
+    double y[kMaxSpace];
+#pragma unroll
+    for (int j = 0; j < kMaxSpace; j++) y[j] = ys[(long long)it.prob * kNP + j];
+    long long end = min(it.start + (long long)kVecChunk, p.ndet);
+    for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) {
+        double x = 0.0;
+#pragma unroll
+        for (int j = 0; j < kMaxSpace; j++)
+            if (j < k) x += y[j] * p.B[(long long)j * p.ndet + I];
+        p.c_out[I] = x;
+    }
+}
+
+// ------------------------------------------------------------------ driver
+
+int dav_init(ifci_handle_t h, DavBatch &b, cudaStream_t s) {
+    init_kernel<<<b.nprob, 256, 0, s>>>(b.d_probs, b.d_state);
+    IFCI_LAUNCH_CHECK(h);
+    init_vec_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems);
+    IFCI_LAUNCH_CHECK(h);
+    return IFCI_OK;
+}
+
+int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_plan, int *d_hi, int *d_lo,
+                void *D, void *G, int *h_nactive, cudaStream_t s) {
+    const int nitem = (int)b.vitems.size();
+    const bool mixed = lo_plan != nullptr;
+    const int restart_at = mixed ? std::min(b.max_space, 4) : b.max_space;
+    for (int it = 0; it < b.max_iter + 2; it++) {
+        select_kernel<<<(b.nprob + 127) / 128, 128, 0, s>>>(b.d_state, b.nprob, mixed ? 1 : 0, d_hi, d_lo);
+        IFCI_LAUNCH_CHECK(h);
+        IFCI_TRY(run_sigma(h, hi_plan, IFCI_FP64, D, G, s));
+        if (mixed) IFCI_TRY(run_sigma(h, *lo_plan, b.precision, D, G, s));
+        dots_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);
+        IFCI_LAUNCH_CHECK(h);
+        solve_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_gs, b.d_y);
+        IFCI_LAUNCH_CHECK(h);
+        residual_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, b.d_part);
+        IFCI_LAUNCH_CHECK(h);
+        IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_nactive, 0, sizeof(int), s));
+        // the restart kernel needs the subspace size before check_kernel shrinks it:
+        // it is always restart_at when a restart happens
+        check_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_coef, b.d_y, b.d_gs, b.max_space,
+                                            restart_at, mixed ? 1 : 0, b.max_iter, b.e_tol, b.r_tol, b.d_nactive);
+        IFCI_LAUNCH_CHECK(h);
+        restart_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, restart_at,
+                                             mixed ? 1 : 0);
+        IFCI_LAUNCH_CHECK(h);
+        for (int pass = 0; pass < 2; pass++) {
+            ortho_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_coef, b.max_space, b.d_part);
+            IFCI_LAUNCH_CHECK(h);
+            reduce_coef_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_coef);
+            IFCI_LAUNCH_CHECK(h);
+        }
+        normalize_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.max_space);
+        IFCI_LAUNCH_CHECK(h);
+        advance_kernel<<<(b.nprob + 127) / 128, 128, 0, s>>>(b.d_probs, b.d_state, b.nprob, b.r_tol);
+        IFCI_LAUNCH_CHECK(h);
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(h_nactive, b.d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+        IFCI_CUDA_TRY(h, cudaStreamSynchronize(s));
+        if (*h_nactive == 0) break;
+    }
+    ritz_out_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y);
+    IFCI_LAUNCH_CHECK(h);
+    return IFCI_OK;
+}
+
+}  // namespace ifci

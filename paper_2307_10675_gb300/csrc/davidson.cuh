@@ -1,0 +1,53 @@
+// Batched Davidson over many CI problems of uneven size.
+#pragma once
+#include "sigma.cuh"
+
+namespace ifci {
+
+struct DavProb {
+    long long ndet;
+    int nstr;
+    int item0, nitem;        // range of vector work items
+    int pad_;
+    double *B;               // (max_space + 1) slots of ndet: basis vectors
+    double *S;               // (max_space + 1) slots of ndet: sigma of each slot
+    const double *hd;        // diagonal <I|H|I> (no constant)
+    double *c_out;           // converged vector or nullptr
+    double e_core;
+};
+
+struct DavState {
+    int k;                   // basis vectors held (slots 0..k-1)
+    int newest;              // slot whose sigma is built next (k - 1)
+    int active;              // 1 while iterating
+    int restart;             // restart requested this iteration
+    int iters;               // sigma builds so far
+    int status;
+    int tslot;               // slot holding the correction vector
+    int ref;                 // index of the closed-shell starting determinant
+    double theta, theta_prev, rnorm, tnorm2, energy;
+};
+
+constexpr int kVecChunk = 4096;   // determinants per vector work item
+constexpr int kMaxSpace = 24;
+constexpr int kNP = kMaxSpace + 2;
+
+struct DavBatch {
+    int nprob = 0, max_space = 12;
+    int precision = IFCI_FP64;
+    int max_iter = 100;
+    double e_tol = 1e-10, r_tol = 1e-6;
+    std::vector<DavProb> probs;
+    std::vector<WorkItem> vitems;
+    DavProb *d_probs = nullptr;
+    DavState *d_state = nullptr;
+    WorkItem *d_vitems = nullptr;
+    double *d_part = nullptr;     // [nitem][kNP]
+    double *d_gs = nullptr;       // [nprob][kMaxSpace*kMaxSpace]
+    double *d_y = nullptr;        // [nprob][kNP]
+    double *d_coef = nullptr;     // [nprob][kNP]
+    int *d_nactive = nullptr;
+};
+
+
+}  // namespace ifci

@@ -1,0 +1,306 @@
+// The iFCI expansion (Methods, Eqs. 1-5): body sets, frozen-body CI problems,
+// batched Davidson, and the FP64 increments eps_X with their sum.
+#include <algorithm>
+#include <cmath>
+
+#include "dav_driver.cuh"
+#include "hamiltonian.cuh"
+
+namespace ifci {
+
+// All body sets of size 1..max_order: by size, then lexicographic.
+static void enumerate_subsets(int nbody, int max_order, std::vector<std::vector<int>> &out) {
+    out.clear();
+    for (int k = 1; k <= max_order; k++) {
+        std::vector<int> c(k);
+        for (int i = 0; i < k; i++) c[i] = i;
+        while (true) {
+            out.push_back(c);
+            int i = k - 1;
+            while (i >= 0 && c[i] == nbody - k + i) i--;
+            if (i < 0) break;
+            c[i]++;
+            for (int j = i + 1; j < k; j++) c[j] = c[j - 1] + 1;
+        }
+    }
+}
+
+// eps_X = sum over non-empty Y subset of X of (-1)^(|X|-|Y|) (E_Y - E_0)
+// (the solution of Eqs. 2-5).  sub_idx lists, for each X, the positions of
+// its subsets; sub_sgn the matching signs.
+__global__ void increments_kernel(int nsub, const long long *__restrict__ sub_off, const int *__restrict__ sub_idx,
+                                  const signed char *__restrict__ sub_sgn, const double *__restrict__ ex,
+                                  const double *__restrict__ e0, double *__restrict__ eps) {
+    int X = blockIdx.x * blockDim.x + threadIdx.x;
+    if (X >= nsub) return;
+    const double E0 = *e0;
+    double v = 0.0;
+    for (long long t = sub_off[X]; t < sub_off[X + 1]; t++) v += (double)sub_sgn[t] * (ex[sub_idx[t]] - E0);
+    eps[X] = v;
+}
+
+// E_total = E_0 + sum_X eps_X, compensated summation in a fixed order.
+__global__ void total_kernel(int nsub, const double *__restrict__ eps, const double *__restrict__ e0,
+                             double *__restrict__ total) {
+    if (threadIdx.x || blockIdx.x) return;
+    double s = 0.0, c = 0.0;
+    for (int i = 0; i < nsub; i++) {
+        double y = eps[i] - c;
+        double t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    *total = *e0 + s;
+}
+
+struct SystemView {
+    const double *h = nullptr, *V = nullptr;   // device
+};
+
+static int validate_system(ifci_handle_t h, const ifci_system_t *sys, int max_order) {
+    if (!sys || !sys->body_offset || !sys->h || !sys->eri || sys->nbody < 1)
+        return set_error(h, IFCI_ERR_INVALID_ARG, "system: null field");
+    if (max_order < 1 || max_order > sys->nbody)
+        return set_error(h, IFCI_ERR_INVALID_ARG, "system: max_order %d with %d bodies", max_order, sys->nbody);
+    if (sys->body_offset[0] != 0 || sys->body_offset[sys->nbody] != sys->norb)
+        return set_error(h, IFCI_ERR_INVALID_ARG, "system: body_offset must run from 0 to norb");
+    for (int b = 0; b < sys->nbody; b++)
+        if (sys->body_offset[b + 1] <= sys->body_offset[b])
+            return set_error(h, IFCI_ERR_INVALID_ARG, "system: body %d has no orbitals", b);
+    return IFCI_OK;
+}
+
+struct SubsetPlan {
+    std::vector<std::vector<int>> subsets;
+    std::vector<int> nA, nC;
+    std::vector<int> orbs;          // per subset: active..., core...
+    std::vector<long long> orb_off;
+    std::vector<long long> sub_off;
+    std::vector<int> sub_idx;
+    std::vector<signed char> sub_sgn;
+};
+
+static void plan_subsets(const ifci_system_t *sys, int max_order, SubsetPlan &P) {
+    enumerate_subsets(sys->nbody, max_order, P.subsets);
+    const int ns = (int)P.subsets.size();
+    // position lookup of a subset: per size, lexicographic rank
+    std::vector<long long> size_off(max_order + 2, 0);
+    for (int k = 1; k <= max_order; k++) size_off[k + 1] = size_off[k] + binom(sys->nbody, k);
+    auto rank_of = [&](const std::vector<int> &Y) -> long long {
+        // lexicographic rank among |Y|-subsets of nbody
+        int k = (int)Y.size(), N = sys->nbody;
+        long long r = 0;
+        int prev = -1;
+        for (int i = 0; i < k; i++) {
+            for (int v = prev + 1; v < Y[i]; v++) r += binom(N - 1 - v, k - 1 - i);
+            prev = Y[i];
+        }
+        return size_off[k] + r;
+    };
+    P.sub_off.assign(1, 0);
+    for (int x = 0; x < ns; x++) {
+        const std::vector<int> &X = P.subsets[x];
+        const int k = (int)X.size();
+        std::vector<char> in(sys->nbody, 0);
+        for (int b : X) in[b] = 1;
+        P.orb_off.push_back((long long)P.orbs.size());
+        int na = 0;
+        for (int b = 0; b < sys->nbody; b++)
+            if (in[b])
+                for (int p = sys->body_offset[b]; p < sys->body_offset[b + 1]; p++, na++) P.orbs.push_back(p);
+        int nc = 0;
+        for (int b = 0; b < sys->nbody; b++)
+            if (!in[b]) { P.orbs.push_back(sys->body_offset[b]); nc++; }
+        P.nA.push_back(na);
+        P.nC.push_back(nc);
+        for (int mask = 1; mask < (1 << k); mask++) {
+            std::vector<int> Y;
+            for (int i = 0; i < k; i++)
+                if (mask >> i & 1) Y.push_back(X[i]);
+            P.sub_idx.push_back((int)rank_of(Y));
+            P.sub_sgn.push_back(((k - (int)Y.size()) & 1) ? -1 : 1);
+        }
+        P.sub_off.push_back((long long)P.sub_idx.size());
+    }
+}
+
+}  // namespace ifci
+
+extern "C" {
+
+int ifci_num_subsets(int nbody, int max_order, long long *count) {
+    if (nbody < 1 || max_order < 1 || max_order > nbody || !count) return IFCI_ERR_INVALID_ARG;
+    long long c = 0;
+    for (int k = 1; k <= max_order; k++) c += ifci::binom(nbody, k);
+    *count = c;
+    return IFCI_OK;
+}
+
+int ifci_increments(ifci_handle_t h, const ifci_system_t *sys, int max_order, const ifci_davidson_opts_t *opts,
+                    double *e0, double *e_x, double *eps, double *e_total, int *status, ifci_stream_t stream) {
+    using namespace ifci;
+    if (!h) return IFCI_ERR_INVALID_ARG;
+    IFCI_TRY(validate_system(h, sys, max_order));
+    if (!e0 || !eps || !e_total) return set_error(h, IFCI_ERR_INVALID_ARG, "increments: null output");
+    ifci_davidson_opts_t o;
+    ifci_davidson_default_opts(&o);
+    if (opts) o = *opts;
+    IFCI_TRY(check_opts(h, o));
+    IFCI_CUDA_TRY(h, cudaSetDevice(h->device));
+    cudaStream_t s = as_cuda(stream);
+    const int norb = sys->norb;
+    for (int b = 0; b < sys->nbody; b++)
+        if (sys->body_offset[b + 1] - sys->body_offset[b] > kMaxNorb)
+            return set_error(h, IFCI_ERR_INVALID_ARG, "increments: body %d too large", b);
+    const long long npg = (long long)norb * (norb + 1) / 2;
+    SubsetPlan P;
+    plan_subsets(sys, max_order, P);
+    const int ns = (int)P.subsets.size();
+    for (int x = 0; x < ns; x++)
+        if (P.nA[x] > kMaxNorb || binom(P.nA[x], (int)P.subsets[x].size()) >= kMaxStr)
+            return set_error(h, IFCI_ERR_INVALID_ARG, "increments: body set %d has %d active orbitals", x, P.nA[x]);
+
+    // keep the converged vectors for the backward pass
+    const bool keep = o.refine >= 0;
+    std::vector<long long> vec_off(ns + 1, 0);
+    for (int x = 0; x < ns; x++) {
+        long long nstr = binom(P.nA[x], (int)P.subsets[x].size());
+        vec_off[x + 1] = vec_off[x] + nstr * nstr;
+    }
+    if (keep) {
+        size_t need = (size_t)vec_off[ns] * 8;
+        if (h->kept.vec_bytes < need) {
+            IFCI_CUDA_TRY(h, cudaDeviceSynchronize());
+            if (h->kept.vec) cudaFree(h->kept.vec);
+            h->kept.vec = nullptr;
+            h->kept.vec_bytes = 0;
+            cudaError_t e = cudaMalloc(&h->kept.vec, need);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return set_error(h, IFCI_ERR_OOM, "increments: %zu bytes for kept vectors", need);
+            }
+            h->kept.vec_bytes = need;
+        }
+        h->kept.valid = false;
+    }
+
+    // workspace: system copy, frozen-core outputs, subset tables, then Davidson batches
+    size_t fixed = ws_round(ns * sizeof(FrozenDesc)) + ws_round(P.orbs.size() * 4) + ws_round((size_t)ns * 8) * 3 +
+                   ws_round(8) * 2 + ws_round((ns + 1) * 8) + ws_round(P.sub_idx.size() * 4) +
+                   ws_round(P.sub_sgn.size()) + ws_round(sys->nbody * 4);
+    if (sys->on_host) fixed += ws_round((size_t)norb * norb * 8) + ws_round((size_t)npg * npg * 8);
+    std::vector<long long> h1_off(ns + 1, 0), eri_off(ns + 1, 0);
+    for (int x = 0; x < ns; x++) {
+        long long na = P.nA[x], npa = na * (na + 1) / 2;
+        h1_off[x + 1] = h1_off[x] + na * na;
+        eri_off[x + 1] = eri_off[x] + npa * npa;
+    }
+    fixed += ws_round((size_t)h1_off[ns] * 8) + ws_round((size_t)eri_off[ns] * 8);
+
+    // Davidson batches under a vector-memory cap
+    std::vector<ProbSpec> all(ns);
+    for (int x = 0; x < ns; x++) all[x] = ProbSpec{P.nA[x], (int)P.subsets[x].size(), nullptr, nullptr, 0.0, nullptr};
+    const size_t cap = (size_t)120 << 30;
+    std::vector<std::pair<int, int>> batches;
+    size_t dav_max = 0;
+    {
+        int first = 0;
+        size_t acc = 0;
+        for (int x = 0; x < ns; x++) {
+            long long nstr = binom(P.nA[x], (int)P.subsets[x].size());
+            size_t vb = (size_t)(2 * (o.max_space + 1) + 1) * nstr * nstr * 8;
+            if (acc + vb > cap && x > first) {
+                batches.push_back({first, x});
+                first = x;
+                acc = 0;
+            }
+            acc += vb;
+        }
+        batches.push_back({first, ns});
+        for (auto &bt : batches) {
+            std::vector<ProbSpec> sp(all.begin() + bt.first, all.begin() + bt.second);
+            dav_max = std::max(dav_max, dav_workspace_bytes(sp, o));
+        }
+    }
+    IFCI_TRY(ws_reserve(h, fixed + dav_max));
+
+    const double *dh = sys->h, *dV = sys->eri;
+    if (sys->on_host) {
+        double *th = ws_take<double>(h, (size_t)norb * norb);
+        double *tV = ws_take<double>(h, (size_t)npg * npg);
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(th, sys->h, (size_t)norb * norb * 8, cudaMemcpyHostToDevice, s));
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(tV, sys->eri, (size_t)npg * npg * 8, cudaMemcpyHostToDevice, s));
+        dh = th;
+        dV = tV;
+    }
+    auto *d_fd = ws_take<FrozenDesc>(h, ns);
+    int *d_orbs = ws_take<int>(h, P.orbs.size());
+    double *d_ecore = ws_take<double>(h, ns);
+    double *d_ex = ws_take<double>(h, ns);
+    double *d_eps = ws_take<double>(h, ns);
+    double *d_e0 = ws_take<double>(h, 1);
+    double *d_tot = ws_take<double>(h, 1);
+    long long *d_soff = ws_take<long long>(h, ns + 1);
+    int *d_sidx = ws_take<int>(h, P.sub_idx.size());
+    signed char *d_ssgn = ws_take<signed char>(h, P.sub_sgn.size());
+    int *d_bond = ws_take<int>(h, sys->nbody);
+    double *d_h1 = ws_take<double>(h, h1_off[ns]);
+    double *d_eri = ws_take<double>(h, eri_off[ns]);
+    if (!d_fd || !d_orbs || !d_ecore || !d_ex || !d_eps || !d_e0 || !d_tot || !d_soff || !d_sidx || !d_ssgn ||
+        !d_bond || !d_h1 || !d_eri)
+        return set_error(h, IFCI_ERR_OOM, "increments: workspace");
+    std::vector<FrozenDesc> fd(ns);
+    for (int x = 0; x < ns; x++)
+        fd[x] = FrozenDesc{P.nA[x], P.nC[x], P.orb_off[x], d_h1 + h1_off[x], d_eri + eri_off[x], d_ecore + x};
+    std::vector<int> bond(sys->nbody);
+    for (int b = 0; b < sys->nbody; b++) bond[b] = sys->body_offset[b];
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_fd, fd.data(), ns * sizeof(FrozenDesc), cudaMemcpyHostToDevice, s));
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_orbs, P.orbs.data(), P.orbs.size() * 4, cudaMemcpyHostToDevice, s));
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_soff, P.sub_off.data(), (ns + 1) * 8, cudaMemcpyHostToDevice, s));
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_sidx, P.sub_idx.data(), P.sub_idx.size() * 4, cudaMemcpyHostToDevice, s));
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_ssgn, P.sub_sgn.data(), P.sub_sgn.size(), cudaMemcpyHostToDevice, s));
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_bond, bond.data(), sys->nbody * 4, cudaMemcpyHostToDevice, s));
+    IFCI_TRY(launch_frozen_core(h, ns, d_fd, d_orbs, dh, dV, norb, s));
+    IFCI_TRY(launch_reference_energy(h, d_bond, sys->nbody, dh, dV, norb, d_e0, s));
+    std::vector<double> ecore(ns);
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(ecore.data(), d_ecore, ns * 8, cudaMemcpyDeviceToHost, s));
+    IFCI_CUDA_TRY(h, cudaStreamSynchronize(s));
+
+    std::vector<double> ex(ns, 0.0);
+    std::vector<int> st(ns, IFCI_OK), its(ns, 0);
+    int ret = IFCI_OK;
+    const size_t mark = h->ws_top;
+    for (auto &bt : batches) {
+        std::vector<ProbSpec> sp;
+        for (int x = bt.first; x < bt.second; x++)
+            sp.push_back(ProbSpec{P.nA[x], (int)P.subsets[x].size(), d_h1 + h1_off[x], d_eri + eri_off[x], ecore[x],
+                                  keep ? h->kept.vec + vec_off[x] : nullptr});
+        h->ws_top = mark;
+        int r = dav_solve(h, sp, o, ex.data() + bt.first, its.data() + bt.first, st.data() + bt.first, s);
+        if (r != IFCI_OK && r != IFCI_ERR_NOT_CONVERGED) return r;
+        if (r != IFCI_OK) ret = r;
+    }
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_ex, ex.data(), ns * 8, cudaMemcpyHostToDevice, s));
+    increments_kernel<<<(ns + 127) / 128, 128, 0, s>>>(ns, d_soff, d_sidx, d_ssgn, d_ex, d_e0, d_eps);
+    IFCI_LAUNCH_CHECK(h);
+    total_kernel<<<1, 32, 0, s>>>(ns, d_eps, d_e0, d_tot);
+    IFCI_LAUNCH_CHECK(h);
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(eps, d_eps, ns * 8, cudaMemcpyDeviceToHost, s));
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(e0, d_e0, 8, cudaMemcpyDeviceToHost, s));
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(e_total, d_tot, 8, cudaMemcpyDeviceToHost, s));
+    IFCI_CUDA_TRY(h, cudaStreamSynchronize(s));
+    if (e_x) std::copy(ex.begin(), ex.end(), e_x);
+    if (status) std::copy(st.begin(), st.end(), status);
+    if (keep) {
+        h->kept.valid = true;
+        h->kept.nbody = sys->nbody;
+        h->kept.max_order = max_order;
+        h->kept.norb = norb;
+        h->kept.body_offset.assign(sys->body_offset, sys->body_offset + sys->nbody + 1);
+        h->kept.vec_off = vec_off;
+    }
+    if (ret != IFCI_OK) set_error(h, ret, "increments: some body sets did not converge");
+    return ret;
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+// Sigma build sigma = H c for a batch of CI problems (Knowles–Handy-style
+// resolution of the identity over singly excited determinants):
+//
+//   D[A][K] = <K| E+_A |c>          gather over K's own alpha and beta excitations
+//   G[A][K] = sum_B W[A][B] D[B][K]  dense contraction (W folds h1 into the ERIs)
+//   sigma_I = sum_A <I| E+_A |K> G[A][K]   gather over I's own excitations
+//
+// E+_pq = E_pq + E_qp (p != q), E+_pp = E_pp.  Each string's excitation list
+// holds at most one entry per pair, sorted by pair, so D rows are built by a
+// merge of the alpha and beta lists with no atomics, and sigma is a gather.
+// D and G are pair-major planes [A][K] so that the alpha parts (whole rows
+// c[J_alpha][:]) are read and written with consecutive K across a warp.
+#include "sigma.cuh"
+
+namespace ifci {
+
+size_t sigma_elem_bytes(int precision) { return precision == IFCI_FP64 ? 8 : 4; }
+
+template <typename TD>
+__global__ void __launch_bounds__(kGatherChunk)
+gather_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__ items, TD *__restrict__ D) {
+    const WorkItem it = items[blockIdx.x];
+    const SigmaProb &p = probs[it.prob];
+    if (p.active && !*p.active) return;
+    const long long K = it.start + threadIdx.x;
+    if (K >= p.ndet) return;
+    const int nstr = p.nstr, nexc = p.nexc, np = p.np;
+    const long long ndet = p.ndet;
+    const int ka = (int)(K / nstr), kb = (int)(K % nstr);
+    const double *__restrict__ c = p.cbase + (p.cslot ? (long long)*p.cslot : 0ll) * p.stride;
+    const int32_t *__restrict__ ea = p.exc + (size_t)ka * nexc;
+    const int32_t *__restrict__ eb = p.exc + (size_t)kb * nexc;
+    int ia = 0, ib = 0;
+    int32_t xa = ea[0], xb = eb[0];
+    int pa = exc_pair(xa), pb = exc_pair(xb);
+    TD *__restrict__ out = D + p.doff + K;
+    const double *crow = c + (long long)ka * nstr;
+    for (int A = 0; A < np; A++) {
+        double v = 0.0;
+        if (pa == A) {
+            v += exc_sign(xa) * c[(long long)exc_J(xa) * nstr + kb];
+            if (++ia < nexc) { xa = ea[ia]; pa = exc_pair(xa); } else pa = -1;
+        }
+        if (pb == A) {
+            v += exc_sign(xb) * crow[exc_J(xb)];
+            if (++ib < nexc) { xb = eb[ib]; pb = exc_pair(xb); } else pb = -1;
+        }
+        out[(long long)A * ndet] = (TD)v;
+    }
+}
+
+// G = W D on CUDA cores (FP64 or FP32), 64x64 output tiles, K step 16.
+template <typename T>
+__global__ void __launch_bounds__(256)
+contract_simt_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__ tiles,
+                     const T *__restrict__ D, T *__restrict__ G) {
+    const WorkItem t = tiles[blockIdx.x];
+    const SigmaProb &p = probs[t.prob];
+    if (p.active && !*p.active) return;
+    const T *__restrict__ W;
+    if constexpr (sizeof(T) == 8) W = reinterpret_cast<const T *>(p.W); else W = reinterpret_cast<const T *>(p.Wf);
+    const int np = p.np, ld = p.ld;
+    const long long ndet = p.ndet;
+    const int m0 = t.sub;
+    const long long n0 = t.start;
+    __shared__ T As[kGemmTK][kGemmTM];
+    __shared__ T Bs[kGemmTK][kGemmTN];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = T(0);
+    const T *Dp = D + p.doff;
+    for (int k0 = 0; k0 < np; k0 += kGemmTK) {
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            int e = threadIdx.x + 256 * r;       // 0..1023
+            int kk = e % kGemmTK, mm = e / kGemmTK;
+            int m = m0 + mm, k = k0 + kk;
+            As[kk][mm] = (m < np && k < np) ? W[(long long)m * ld + k] : T(0);
+            int nn = e % kGemmTN, kb = e / kGemmTN;
+            long long n = n0 + nn;
+            int kr = k0 + kb;
+            Bs[kb][nn] = (n < ndet && kr < np) ? Dp[(long long)kr * ndet + n] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kGemmTK; kk++) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    T *Gp = G + p.doff;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        int m = m0 + ty * 4 + i;
+        if (m >= np) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            long long n = n0 + tx + 16 * j;
+            if (n < ndet) Gp[(long long)m * ndet + n] = acc[i][j];
+        }
+    }
+}
+
+template <typename TG>
+__global__ void __launch_bounds__(kGatherChunk)
+scatter_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__ items, const TG *__restrict__ G) {
+    const WorkItem it = items[blockIdx.x];
+    const SigmaProb &p = probs[it.prob];
+    if (p.active && !*p.active) return;
+    const long long I = it.start + threadIdx.x;
+    if (I >= p.ndet) return;
+    const int nstr = p.nstr, nexc = p.nexc;
+    const long long ndet = p.ndet;
+    const int ia = (int)(I / nstr), ib = (int)(I % nstr);
+    const int32_t *__restrict__ ea = p.exc + (size_t)ia * nexc;
+    const int32_t *__restrict__ eb = p.exc + (size_t)ib * nexc;
+    const TG *__restrict__ Gp = G + p.doff;
+    double v = 0.0;
+    for (int e = 0; e < nexc; e++) {
+        int32_t x = ea[e];
+        v += exc_sign(x) * (double)Gp[(long long)exc_pair(x) * ndet + (long long)exc_J(x) * nstr + ib];
+    }
+    const long long rowb = (long long)ia * nstr;
+    for (int e = 0; e < nexc; e++) {
+        int32_t x = eb[e];
+        v += exc_sign(x) * (double)Gp[(long long)exc_pair(x) * ndet + rowb + exc_J(x)];
+    }
+    double *s = p.sbase + (p.sslot ? (long long)*p.sslot : 0ll) * p.stride;
+    s[I] = v;
+}
+
+int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision) {
+    plan.waves.clear();
+    plan.items.clear();
+    plan.tiles.clear();
+    plan.tctiles.clear();
+    plan.max_delems = 0;
+    const bool tc = precision == IFCI_BF16 || precision == IFCI_TF32;
+    SigmaWave w{0, 0, 0, 0, 0, 0, 0};
+    for (size_t i = 0; i < plan.probs.size(); i++) {
+        SigmaProb &p = plan.probs[i];
+        long long need = (long long)p.np * p.ndet;
+        if (need > budget)
+            return set_error(h, IFCI_ERR_OOM, "sigma: one problem needs %lld intermediate elements, budget %lld",
+                             need, budget);
+        if (w.delems + need > budget) {
+            plan.max_delems = std::max(plan.max_delems, w.delems);
+            plan.waves.push_back(w);
+            w = SigmaWave{(int)plan.items.size(), 0, (int)plan.tiles.size(), 0, (int)plan.tctiles.size(), 0, 0};
+        }
+        p.doff = w.delems;
+        w.delems += need;
+        for (long long s0 = 0; s0 < p.ndet; s0 += kGatherChunk) {
+            plan.items.push_back(WorkItem{(int)i, 0, s0});
+            w.nitem++;
+        }
+        if (tc) {
+            // one tile = 128 determinants x all pairs (see sigma_tc.cu)
+            for (long long s0 = 0; s0 < p.ndet; s0 += 128) {
+                plan.tctiles.push_back(WorkItem{(int)i, 0, s0});
+                w.ntc++;
+            }
+        } else {
+            for (int m0 = 0; m0 < p.np; m0 += kGemmTM)
+                for (long long s0 = 0; s0 < p.ndet; s0 += kGemmTN) {
+                    plan.tiles.push_back(WorkItem{(int)i, m0, s0});
+                    w.ntile++;
+                }
+        }
+    }
+    if (w.nitem) {
+        plan.max_delems = std::max(plan.max_delems, w.delems);
+        plan.waves.push_back(w);
+    }
+    return IFCI_OK;
+}
+
+size_t plan_device_bytes(const SigmaPlan &plan) {
+    return ws_round(plan.probs.size() * sizeof(SigmaProb)) + ws_round(plan.items.size() * sizeof(WorkItem)) +
+           ws_round(plan.tiles.size() * sizeof(WorkItem)) + ws_round(plan.tctiles.size() * sizeof(WorkItem));
+}
+
+int upload_plan(ifci_handle_t h, SigmaPlan &plan, cudaStream_t s) {
+    plan.d_probs = ws_take<SigmaProb>(h, std::max<size_t>(1, plan.probs.size()));
+    plan.d_items = ws_take<WorkItem>(h, std::max<size_t>(1, plan.items.size()));
+    plan.d_tiles = ws_take<WorkItem>(h, std::max<size_t>(1, plan.tiles.size()));
+    plan.d_tctiles = ws_take<WorkItem>(h, std::max<size_t>(1, plan.tctiles.size()));
+    if (!plan.d_probs || !plan.d_items || !plan.d_tiles || !plan.d_tctiles)
+        return set_error(h, IFCI_ERR_OOM, "sigma plan: workspace too small");
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(plan.d_probs, plan.probs.data(), plan.probs.size() * sizeof(SigmaProb),
+                                     cudaMemcpyHostToDevice, s));
+    if (!plan.items.empty())
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(plan.d_items, plan.items.data(), plan.items.size() * sizeof(WorkItem),
+                                         cudaMemcpyHostToDevice, s));
+    if (!plan.tiles.empty())
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(plan.d_tiles, plan.tiles.data(), plan.tiles.size() * sizeof(WorkItem),
+                                         cudaMemcpyHostToDevice, s));
+    if (!plan.tctiles.empty())
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(plan.d_tctiles, plan.tctiles.data(),
+                                         plan.tctiles.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+    return IFCI_OK;
+}
+
+int run_sigma(ifci_handle_t h, const SigmaPlan &plan, int precision, void *D, void *G, cudaStream_t s) {
+    for (const SigmaWave &w : plan.waves) {
+        if (w.nitem == 0) continue;
+        if (precision == IFCI_FP64) {
+            gather_kernel<double><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0, (double *)D);
+            IFCI_LAUNCH_CHECK(h);
+            contract_simt_kernel<double><<<w.ntile, 256, 0, s>>>(plan.d_probs, plan.d_tiles + w.tile0,
+                                                                 (const double *)D, (double *)G);
+            IFCI_LAUNCH_CHECK(h);
+            scatter_kernel<double><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
+                                                                    (const double *)G);
+            IFCI_LAUNCH_CHECK(h);
+        } else if (precision == IFCI_FP32) {
+            gather_kernel<float><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0, (float *)D);
+            IFCI_LAUNCH_CHECK(h);
+            contract_simt_kernel<float><<<w.ntile, 256, 0, s>>>(plan.d_probs, plan.d_tiles + w.tile0,
+                                                               (const float *)D, (float *)G);
+            IFCI_LAUNCH_CHECK(h);
+            scatter_kernel<float><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
+                                                                   (const float *)G);
+            IFCI_LAUNCH_CHECK(h);
+        } else {
+            IFCI_TRY(launch_tc_contract(h, plan, w, precision, D, G, s));
+            scatter_kernel<float><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
+                                                                   (const float *)G);
+            IFCI_LAUNCH_CHECK(h);
+        }
+    }
+    return IFCI_OK;
+}
+
+// FP32 copy of the folded matrix for the FP32 path.
+__global__ void convert_w_kernel(const SigmaProb *__restrict__ probs) {
+    const SigmaProb &p = probs[blockIdx.x];
+    float *Wf = const_cast<float *>(p.Wf);
+    for (long long t = threadIdx.x; t < (long long)p.ld * p.ld; t += blockDim.x) Wf[t] = (float)p.W[t];
+}
+
+int launch_convert_w(ifci_handle_t h, int nprob, const SigmaProb *d_probs, cudaStream_t s) {
+    convert_w_kernel<<<nprob, 256, 0, s>>>(d_probs);
+    IFCI_LAUNCH_CHECK(h);
+    return IFCI_OK;
+}
+
+}  // namespace ifci

@@ -1,0 +1,72 @@
+// Batched sigma build: gather D = E+ c, contraction G = W D, scatter sigma = E+ G.
+#pragma once
+#include "common.cuh"
+
+namespace ifci {
+
+// One CI problem as seen by the sigma kernels.  The input vector is
+// cbase + (*cslot) * stride and the output sbase + (*sslot) * stride, so a
+// Davidson iteration can move its slots on the device.
+struct SigmaProb {
+    int n, nstr, nexc, np;   // active orbitals, strings, excitations per string, pairs
+    int ld;                  // row stride of W (>= np)
+    int pad_;
+    long long ndet;
+    long long stride;
+    const int32_t *exc;      // [nstr * nexc] excitation table of (n, nelec_spin)
+    const double *W;         // [ld * ld] folded contraction matrix, FP64
+    const float *Wf;         // [ld * ld] FP32 copy (FP32 path) or nullptr
+    const void *Wtc;         // tensor-core operand image (BF16/TF32 paths) or nullptr
+    const double *cbase;
+    double *sbase;
+    const int *cslot;        // device slot index or nullptr (= 0)
+    const int *sslot;        // device slot index or nullptr (= 0)
+    const int *active;       // device flag or nullptr (= active)
+    long long doff;          // element offset of this problem's D and G blocks in a wave
+};
+
+struct WorkItem {
+    int prob;
+    int sub;                 // GEMM: first output pair row of the tile
+    long long start;         // first determinant
+};
+
+constexpr int kGatherChunk = 256;   // determinants per gather/scatter block
+constexpr int kGemmTM = 64, kGemmTN = 64, kGemmTK = 16;
+
+struct SigmaWave {
+    int item0, nitem;        // gather/scatter items
+    int tile0, ntile;        // contraction tiles
+    int tc0, ntc;            // tensor-core tiles (BF16/TF32)
+    long long delems;        // D (and G) elements of the wave
+};
+
+// Host-side plan over a fixed problem set; device arrays live in caller memory.
+struct SigmaPlan {
+    std::vector<SigmaProb> probs;
+    std::vector<SigmaWave> waves;
+    std::vector<WorkItem> items, tiles, tctiles;
+    long long max_delems = 0;
+    SigmaProb *d_probs = nullptr;
+    WorkItem *d_items = nullptr, *d_tiles = nullptr, *d_tctiles = nullptr;
+};
+
+// Splits probs into waves of at most `budget` D elements (each problem whole).
+// Fails if one problem alone exceeds the budget.
+int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision);
+size_t plan_device_bytes(const SigmaPlan &plan);
+// Copies the plan's descriptor arrays to device memory taken from the workspace.
+int upload_plan(ifci_handle_t h, SigmaPlan &plan, cudaStream_t s);
+// Launches every wave: D, G are device buffers of at least max_delems
+// elements of the precision's storage type (8 B for FP64, 4 B otherwise).
+int run_sigma(ifci_handle_t h, const SigmaPlan &plan, int precision, void *D, void *G, cudaStream_t s);
+size_t sigma_elem_bytes(int precision);
+
+// tensor-core contraction (sigma_tc.cu)
+int tc_supported(int precision);
+int tc_operand_bytes(int np, int precision);   // bytes of one problem's W image
+int launch_tc_pack_w(ifci_handle_t h, int nprob, const SigmaProb *d_probs, int precision, cudaStream_t s);
+int launch_tc_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &w, int precision,
+                       const void *D, void *G, cudaStream_t s);
+
+}  // namespace ifci
