@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the iFCI increment CI solve on one GB300 (or N, one rank each).
+
+One step = the whole hot path over one synthetic workload: every body set of
+the 24-body uneven chain up to 3 bodies (24 + 276 + 2024 = 2324 CI problems,
+largest CAS(6e,18o) with 665,856 determinants), frozen-body Hamiltonians,
+batched Davidson to convergence, and the FP64 increments with their sum,
+all through ``ifci_increments`` with device-resident integrals.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "iFCI increments/s & sigma TFLOP/s, 1 GB300, batched+mixed vs plain FP64 @1µEh"
+UNIT = "increments/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--max-order", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sample-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- workload
+
+def workload(rank: int = 0):
+    from synth import chain_24_uneven
+    # weak scaling: rank r solves its own chain (seed 2308 + r) of the same shape
+    return chain_24_uneven(seed=2308 + rank)
+
+
+def cost_of(n: int, m: int):
+    """(determinants, sigma contraction FLOPs 2*ndet*npair^2) of one CI problem."""
+    nd = math.comb(n, m) ** 2
+    npair = n * (n + 1) // 2
+    return nd, 2.0 * nd * npair * npair
+
+
+def subset_sizes(chain, max_order):
+    import itertools
+    out = []
+    for k in range(1, max_order + 1):
+        for X in itertools.combinations(range(chain.nbody), k):
+            out.append((X, sum(chain.body_sizes[b] for b in X), k))
+    return out
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle baseline
+
+def oracle_baseline(chain, max_order, seconds, seed=11):
+    """Times the oracle on a seeded sample of the workload's body sets for about
+    ``seconds`` and extrapolates the whole workload's time with the cost model
+    t(X) ~ ndet(X) * connected determinants per row(X)."""
+    from oracle import fci
+    subs = subset_sizes(chain, max_order)
+
+    def conn(n, m):
+        s1 = m * (n - m)
+        s2 = math.comb(m, 2) * math.comb(n - m, 2)
+        return 1 + 2 * (s1 + s2) + s1 * s1
+
+    def model(n, m):
+        return math.comb(n, m) ** 2 * conn(n, m)
+
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(subs))
+    fci.lib()                       # build/load before timing
+    done, t_used, m_used = 0, 0.0, 0.0
+    for idx in order:
+        X, n, k = subs[idx]
+        if math.comb(n, k) ** 2 > 30000:
+            continue
+        t0 = time.perf_counter()
+        fci.solve_subsystem(chain, X)
+        t_used += time.perf_counter() - t0
+        m_used += model(n, k)
+        done += 1
+        if t_used > seconds:
+            break
+    total_model = sum(model(n, k) for _, n, k in subs)
+    t_total = t_used / m_used * total_model
+    return {"value": len(subs) / t_total, "unit": UNIT, "cores": fci.num_threads(), "kind": "oracle",
+            "sample": (f"{done} seeded body sets with <= 30,000 determinants timed in {t_used:.1f} s; "
+                       f"whole-workload time extrapolated by ndet x connections per row "
+                       f"({t_total:.0f} s for {len(subs)} sets)")}
+
+
+# ---------------------------------------------------------------- main
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        steps = args.steps if args.steps is not None else 1
+        chain = workload(0)
+        per = max(3.0, args.sample_seconds / 2)
+        for _ in range(args.warmup):
+            oracle_baseline(chain, args.max_order, per)
+        vals = []
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            r = oracle_baseline(chain, args.max_order, per)
+            vals.append(r["value"])
+        el = time.perf_counter() - t0
+        v = float(np.mean(vals))
+        line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": steps, "warmup": args.warmup,
+                "ms_per_step": 1000 * el / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": "chain-24-uneven, iFCI to 3 bodies, 2324 CI problems, max CAS(6e,18o)",
+                           "seed": chain.seed, "sample": "bounded oracle sample per step"},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                                 "sample": r["sample"]},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    import torch
+    import paper_2307_10675_gb300 as ifci
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    steps = args.steps if args.steps is not None else (1 if args.precision == "fp64" else 5)
+    warmup = max(3, args.warmup)
+
+    chain = workload(rank)
+    sysd = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=dev),
+                             torch.tensor(chain.eri_packed(), device=dev))
+    opts = ifci.davidson_opts(args.precision, r_tol=1e-6, e_tol=1e-10)
+    subs = subset_sizes(chain, args.max_order)
+    nsub = len(subs)
+    handle = ifci.Handle(0, local)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(warmup):
+        out = ifci.ifci_increments(handle, sysd, args.max_order, opts)
+    torch.cuda.synchronize(dev)
+
+    handle.profile_enable(True)
+    l0 = handle.launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        out = ifci.ifci_increments(handle, sysd, args.max_order, opts)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    launches = handle.launches() - l0
+    prof = handle.profile_read()
+    handle.profile_enable(False)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # algorithmic sigma FLOPs of a step: sigma builds per problem x 2 ndet npair^2
+    its = out["iters"]
+    flops_step = 0.0
+    for (X, n, k), it in zip(subs, its):
+        flops_step += it * cost_of(n, k)[1]
+
+    ms_step = ms / steps
+    value = world * nsub / (ms_step / 1000.0)
+    c_ms, c_n = prof["contract"]
+    sig_ms = prof["gather"][0] + prof["contract"][0] + prof["scatter"][0]
+    flops_per_launch = flops_step * steps / max(1, c_n)
+    achieved_tf = flops_step * steps / (c_ms / 1000.0) / 1e12 if c_ms > 0 else None
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    if args.precision == "fp64":
+        fp64_peak, fp64_how = _dgemm_peak(dev)
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": (achieved_tf / fp64_peak) if (achieved_tf and fp64_peak) else None, "traffic": None,
+                "kernel": "contract_simt_kernel<double>", "peak_source": fp64_how,
+                "flops_per_launch": flops_per_launch}
+        dtype = "f64"
+    else:
+        bf = peaks.get("bf16_tflops_sustained", 1700.0)
+        ratio = {"bf16": 1.0, "tf32": 0.5, "fp32": 1.0 / 28.0}[args.precision]
+        pk = bf * ratio
+        roof = {"bound": "tensor", "achieved": achieved_tf, "peak": pk, "unit": "TFLOP/s",
+                "frac": (achieved_tf / pk) if achieved_tf else None, "traffic": None,
+                "peak_source": "MEASURED_PEAKS bf16 sustained x nominal dtype ratio"}
+        dtype = args.precision + "+f64"
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": dtype, "data": "synthetic",
+        "config": {"workload": "chain-24-uneven, iFCI to 3 bodies, 2324 CI problems, max CAS(6e,18o)",
+                   "seed": chain.seed, "bodies": chain.nbody, "orbitals": chain.norb,
+                   "max_order": args.max_order, "precision": args.precision,
+                   "davidson": {"r_tol": 1e-6, "e_tol": 1e-10, "max_space": 12},
+                   "l2": "inputs larger than L2: Davidson vectors of one step ~38 GB",
+                   "parallelism": f"{world} independent chains (one per GPU)"},
+        "sigma_tflops": (flops_step * steps / (sig_ms / 1000.0) / 1e12) if sig_ms > 0 else None,
+        "kernel_ms": {k: v[0] / steps for k, v in prof.items()},
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e_total": out["e_total"],
+    }
+
+    if not args.no_e2e:
+        line["e2e"] = _e2e(ifci, handle, chain, args.max_order, opts, world, nsub, dist, dev)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_baseline(workload(0), args.max_order, args.sample_seconds)
+    handle.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def _dgemm_peak(dev):
+    """cuBLAS DGEMM throughput on this GPU (best of 5, 4096^3) as the FP64 peak."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        torch.matmul(a, b)
+    torch.cuda.synchronize(dev)
+    best = 1e9
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        best = min(best, e0.elapsed_time(e1))
+    tf = 2.0 * n ** 3 / (best / 1000.0) / 1e12
+    return tf, "measured in this run: cuBLAS DGEMM 4096^3 (torch.matmul float64), best of 5"
+
+
+def _e2e(ifci, handle, chain, max_order, opts, world, nsub, dist, dev):
+    """Same metric through the public call with host buffers: the integrals are
+    copied in from pinned host memory and all results come back inside the call."""
+    import torch
+    h_pin = torch.tensor(chain.h).pin_memory()
+    v_pin = torch.tensor(chain.eri_packed()).pin_memory()
+    sysh = ifci.SystemArrays(chain.body_offsets, h_pin.numpy(), v_pin.numpy())
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    out = ifci.ifci_increments(handle, sysh, max_order, opts)
+    torch.cuda.synchronize(dev)
+    el = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([el], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    h2d = h_pin.numel() * 8 + v_pin.numel() * 8
+    d2h = (2 * nsub + 2) * 8 + nsub * 4
+    return {"value": world * nsub / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "e_total": out["e_total"]}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

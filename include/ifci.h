@@ -78,6 +78,15 @@ size_t ifci_workspace_bytes(ifci_handle_t handle);
 /* Number of kernel launches this handle has issued since creation. */
 long long ifci_kernel_launches(ifci_handle_t handle);
 
+/* Per-kernel-class timing with CUDA events recorded on the launching stream
+ * around every kernel the library issues (no paper counterpart; it serves
+ * the roofline measurement).  enable != 0 turns it on and zeroes the totals.
+ * Classes: 0 sigma gather, 1 sigma contraction, 2 sigma scatter,
+ * 3 Davidson vector kernels, 4 other.  ifci_profile_read synchronises the
+ * recorded events and returns the accumulated milliseconds and launches. */
+int ifci_profile_enable(ifci_handle_t handle, int enable);
+int ifci_profile_read(ifci_handle_t handle, int kind, double *ms, long long *launches);
+
 /* ---------------------------------------------------------------- strings */
 
 /* Host-only.  nstr = C(norb, nelec_spin); nexc = excitations per string =
@@ -193,12 +202,13 @@ int ifci_num_subsets(int nbody, int max_order, long long *count);
  *   e_x     : host double[nsub] or NULL, E_X per body set.
  *   eps     : host double[nsub], increments eps_X.
  *   e_total : host double*, E_0 + sum eps_X.
+ *   iters   : host int[nsub] or NULL, sigma builds per set.
  *   status  : host int[nsub] or NULL, per-set Davidson status.
  * Keeps the converged vectors in the handle when opts->refine >= 0 so that
  * ifci_rdm_backward can reuse them.  Synchronous. */
 int ifci_increments(ifci_handle_t handle, const ifci_system_t *sys, int max_order,
                     const ifci_davidson_opts_t *opts, double *e0, double *e_x, double *eps,
-                    double *e_total, int *status, ifci_stream_t stream);
+                    double *e_total, int *iters, int *status, ifci_stream_t stream);
 
 /* ifci_rdm_backward — gradient of E_iFCI (truncated at max_order) with
  * respect to the inputs h and V by Hellmann–Feynman on every E_Y:

@@ -26,8 +26,9 @@ EXPORTS = [
     "ifci_handle_create", "ifci_handle_destroy", "ifci_last_error_string", "ifci_workspace_bytes",
     "ifci_kernel_launches", "ifci_string_counts", "ifci_build_strings", "ifci_sigma", "ifci_hdiag",
     "ifci_frozen_core", "ifci_davidson_default_opts", "ifci_davidson_batched", "ifci_num_subsets",
-    "ifci_increments", "ifci_rdm_backward",
+    "ifci_increments", "ifci_rdm_backward", "ifci_profile_enable", "ifci_profile_read",
 ]
+PROFILE_KINDS = {"gather": 0, "contract": 1, "scatter": 2, "vector": 3, "other": 4}
 
 
 class Strings(ctypes.Structure):
@@ -85,8 +86,10 @@ def load(build_if_missing: bool = True):
                                         c_double_p, c_int_p, c_int_p, c_void_p]
     L.ifci_num_subsets.argtypes = [c_int, c_int, ctypes.POINTER(c_ll)]
     L.ifci_increments.argtypes = [H, ctypes.POINTER(System), c_int, ctypes.POINTER(DavidsonOpts), c_double_p,
-                                  c_double_p, c_double_p, c_double_p, c_int_p, c_void_p]
+                                  c_double_p, c_double_p, c_double_p, c_int_p, c_int_p, c_void_p]
     L.ifci_rdm_backward.argtypes = [H, ctypes.POINTER(System), c_int, ctypes.POINTER(DavidsonOpts), c_double,
                                     c_void_p, c_void_p, c_int, c_void_p]
+    L.ifci_profile_enable.argtypes = [H, c_int]
+    L.ifci_profile_read.argtypes = [H, c_int, c_double_p, ctypes.POINTER(c_ll)]
     _LIB = L
     return L

@@ -70,6 +70,18 @@ class Handle:
     def workspace_bytes(self) -> int:
         return int(_lib().ifci_workspace_bytes(self._h))
 
+    def profile_enable(self, on: bool = True):
+        self.check(_lib().ifci_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """{class: (milliseconds, launches)} of the per-kernel-class event timing."""
+        out = {}
+        for name, k in _capi.PROFILE_KINDS.items():
+            ms, n = ctypes.c_double(), ctypes.c_longlong()
+            self.check(_lib().ifci_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out
+
     def close(self):
         if self._h:
             _lib().ifci_handle_destroy(self._h)
@@ -252,12 +264,14 @@ def ifci_increments(handle: Handle, system: SystemArrays, max_order: int, opts=N
     ex = np.zeros(ns)
     eps = np.zeros(ns)
     st = np.zeros(ns, dtype=np.int32)
+    it = np.zeros(ns, dtype=np.int32)
     o = opts or davidson_opts()
     rc = _lib().ifci_increments(handle.ptr, system.as_c(), max_order, ctypes.byref(o), ctypes.byref(e0),
                                 ex.ctypes.data_as(_capi.c_double_p), eps.ctypes.data_as(_capi.c_double_p),
-                                ctypes.byref(tot), st.ctypes.data_as(_capi.c_int_p), _stream(stream))
+                                ctypes.byref(tot), it.ctypes.data_as(_capi.c_int_p),
+                                st.ctypes.data_as(_capi.c_int_p), _stream(stream))
     handle.check(rc, allow=(IFCI_ERR_NOT_CONVERGED,) if allow_unconverged else ())
-    return {"e0": e0.value, "e_x": ex, "eps": eps, "e_total": tot.value, "status": st}
+    return {"e0": e0.value, "e_x": ex, "eps": eps, "e_total": tot.value, "iters": it, "status": st}
 
 
 def ifci_rdm_backward(handle: Handle, system: SystemArrays, max_order: int, grad_out: float = 1.0, opts=None,

@@ -10,6 +10,13 @@
 
 struct ifci_handle_s {
     int device = 0;
+    // per-kernel-class CUDA-event timing (ifci_profile_enable)
+    bool prof = false;
+    struct ProfRec { cudaEvent_t a, b; int kind; };
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[8] = {0};
+    long long prof_count[8] = {0};
     char *ws = nullptr;          // workspace base (device)
     size_t ws_bytes = 0;         // capacity
     size_t ws_top = 0;           // bump pointer
@@ -68,6 +75,23 @@ int set_error(ifci_handle_t h, int code, const char *fmt, ...);
         int _s = (expr);                \
         if (_s != IFCI_OK) return _s;   \
     } while (0)
+
+// profiling ---------------------------------------------------------------
+enum ProfKind { PK_GATHER = 0, PK_CONTRACT = 1, PK_SCATTER = 2, PK_VECTOR = 3, PK_OTHER = 4 };
+void prof_begin(ifci_handle_t h, cudaStream_t s, int kind);
+void prof_end(ifci_handle_t h, cudaStream_t s);
+void prof_collect(ifci_handle_t h);   // adds finished event pairs to the totals (synchronises them)
+
+struct ProfScope {
+    ifci_handle_t h;
+    cudaStream_t s;
+    ProfScope(ifci_handle_t h_, cudaStream_t s_, int kind) : h(h_), s(s_) {
+        if (h->prof) prof_begin(h, s, kind);
+    }
+    ~ProfScope() {
+        if (h->prof) prof_end(h, s);
+    }
+};
 
 // workspace --------------------------------------------------------------
 // Calls reserve what they need up front (ws_reserve), then carve pieces with

@@ -544,6 +544,7 @@ int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_
         IFCI_LAUNCH_CHECK(h);
         IFCI_TRY(run_sigma(h, hi_plan, IFCI_FP64, D, G, s));
         if (mixed) IFCI_TRY(run_sigma(h, *lo_plan, b.precision, D, G, s));
+        ProfScope vec_scope(h, s, PK_VECTOR);
         dots_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);
         IFCI_LAUNCH_CHECK(h);
         solve_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_gs, b.d_y);
@@ -569,6 +570,7 @@ int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_
         IFCI_LAUNCH_CHECK(h);
         advance_kernel<<<(b.nprob + 127) / 128, 128, 0, s>>>(b.d_probs, b.d_state, b.nprob, b.r_tol);
         IFCI_LAUNCH_CHECK(h);
+        if (h->prof) prof_end(h, s);
         IFCI_CUDA_TRY(h, cudaMemcpyAsync(h_nactive, b.d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
         IFCI_CUDA_TRY(h, cudaStreamSynchronize(s));
         if (*h_nactive == 0) break;

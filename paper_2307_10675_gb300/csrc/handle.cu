@@ -49,6 +49,50 @@ int ws_reserve(ifci_handle_t h, size_t bytes) {
 
 void ws_reset(ifci_handle_t h) { h->ws_top = 0; }
 
+static cudaEvent_t prof_event(ifci_handle_t h) {
+    if (!h->prof_pool.empty()) {
+        cudaEvent_t e = h->prof_pool.back();
+        h->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(ifci_handle_t h, cudaStream_t s, int kind) {
+    ifci_handle_s::ProfRec r;
+    r.a = prof_event(h);
+    r.b = nullptr;
+    r.kind = kind;
+    cudaEventRecord(r.a, s);
+    h->prof_pending.push_back(r);
+}
+
+void prof_end(ifci_handle_t h, cudaStream_t s) {
+    if (h->prof_pending.empty()) return;
+    auto &r = h->prof_pending.back();
+    if (r.b) return;
+    r.b = prof_event(h);
+    cudaEventRecord(r.b, s);
+}
+
+void prof_collect(ifci_handle_t h) {
+    for (auto &r : h->prof_pending) {
+        if (!r.b) continue;
+        cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            h->prof_ms[r.kind] += ms;
+            h->prof_count[r.kind] += 1;
+        }
+        h->prof_pool.push_back(r.a);
+        h->prof_pool.push_back(r.b);
+    }
+    h->prof_pending.clear();
+    cudaGetLastError();
+}
+
 int device_sm_count(int device) {
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device);
@@ -89,6 +133,8 @@ int ifci_handle_destroy(ifci_handle_t h) {
     cudaGetDevice(&prev);
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
+    ifci::prof_collect(h);
+    for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
     if (h->ws) cudaFree(h->ws);
     if (h->kept.vec) cudaFree(h->kept.vec);
     cudaSetDevice(prev);
@@ -101,5 +147,28 @@ const char *ifci_last_error_string(ifci_handle_t h) { return h ? h->last_error.c
 size_t ifci_workspace_bytes(ifci_handle_t h) { return h ? h->ws_bytes : 0; }
 
 long long ifci_kernel_launches(ifci_handle_t h) { return h ? h->launches : 0; }
+
+int ifci_profile_enable(ifci_handle_t h, int enable) {
+    if (!h) return IFCI_ERR_INVALID_ARG;
+    ifci::prof_collect(h);
+    h->prof = enable != 0;
+    for (int k = 0; k < 8; k++) {
+        h->prof_ms[k] = 0.0;
+        h->prof_count[k] = 0;
+    }
+    return IFCI_OK;
+}
+
+int ifci_profile_read(ifci_handle_t h, int kind, double *ms, long long *launches) {
+    if (!h || kind < 0 || kind >= 8) return IFCI_ERR_INVALID_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    ifci::prof_collect(h);
+    cudaSetDevice(prev);
+    if (ms) *ms = h->prof_ms[kind];
+    if (launches) *launches = h->prof_count[kind];
+    return IFCI_OK;
+}
 
 }  // extern "C"

@@ -137,7 +137,8 @@ int ifci_num_subsets(int nbody, int max_order, long long *count) {
 }
 
 int ifci_increments(ifci_handle_t h, const ifci_system_t *sys, int max_order, const ifci_davidson_opts_t *opts,
-                    double *e0, double *e_x, double *eps, double *e_total, int *status, ifci_stream_t stream) {
+                    double *e0, double *e_x, double *eps, double *e_total, int *iters, int *status,
+                    ifci_stream_t stream) {
     using namespace ifci;
     if (!h) return IFCI_ERR_INVALID_ARG;
     IFCI_TRY(validate_system(h, sys, max_order));
@@ -291,6 +292,7 @@ int ifci_increments(ifci_handle_t h, const ifci_system_t *sys, int max_order, co
     IFCI_CUDA_TRY(h, cudaStreamSynchronize(s));
     if (e_x) std::copy(ex.begin(), ex.end(), e_x);
     if (status) std::copy(st.begin(), st.end(), status);
+    if (iters) std::copy(its.begin(), its.end(), iters);
     if (keep) {
         h->kept.valid = true;
         h->kept.nbody = sys->nbody;

@@ -216,25 +216,42 @@ int run_sigma(ifci_handle_t h, const SigmaPlan &plan, int precision, void *D, vo
     for (const SigmaWave &w : plan.waves) {
         if (w.nitem == 0) continue;
         if (precision == IFCI_FP64) {
-            gather_kernel<double><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0, (double *)D);
-            IFCI_LAUNCH_CHECK(h);
-            contract_simt_kernel<double><<<w.ntile, 256, 0, s>>>(plan.d_probs, plan.d_tiles + w.tile0,
-                                                                 (const double *)D, (double *)G);
-            IFCI_LAUNCH_CHECK(h);
+            {
+                ProfScope ps(h, s, PK_GATHER);
+                gather_kernel<double><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
+                                                                       (double *)D);
+                IFCI_LAUNCH_CHECK(h);
+            }
+            {
+                ProfScope ps(h, s, PK_CONTRACT);
+                contract_simt_kernel<double><<<w.ntile, 256, 0, s>>>(plan.d_probs, plan.d_tiles + w.tile0,
+                                                                     (const double *)D, (double *)G);
+                IFCI_LAUNCH_CHECK(h);
+            }
+            ProfScope ps(h, s, PK_SCATTER);
             scatter_kernel<double><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
                                                                     (const double *)G);
             IFCI_LAUNCH_CHECK(h);
         } else if (precision == IFCI_FP32) {
-            gather_kernel<float><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0, (float *)D);
-            IFCI_LAUNCH_CHECK(h);
-            contract_simt_kernel<float><<<w.ntile, 256, 0, s>>>(plan.d_probs, plan.d_tiles + w.tile0,
-                                                               (const float *)D, (float *)G);
-            IFCI_LAUNCH_CHECK(h);
+            {
+                ProfScope ps(h, s, PK_GATHER);
+                gather_kernel<float><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
+                                                                      (float *)D);
+                IFCI_LAUNCH_CHECK(h);
+            }
+            {
+                ProfScope ps(h, s, PK_CONTRACT);
+                contract_simt_kernel<float><<<w.ntile, 256, 0, s>>>(plan.d_probs, plan.d_tiles + w.tile0,
+                                                                   (const float *)D, (float *)G);
+                IFCI_LAUNCH_CHECK(h);
+            }
+            ProfScope ps(h, s, PK_SCATTER);
             scatter_kernel<float><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
                                                                    (const float *)G);
             IFCI_LAUNCH_CHECK(h);
         } else {
             IFCI_TRY(launch_tc_contract(h, plan, w, precision, D, G, s));
+            ProfScope ps(h, s, PK_SCATTER);
             scatter_kernel<float><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
                                                                    (const float *)G);
             IFCI_LAUNCH_CHECK(h);
