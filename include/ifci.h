@@ -127,6 +127,29 @@ int ifci_sigma(ifci_handle_t handle, const ifci_strings_t *str,
                const double *h1, const double *eri, const double *c, double *sigma,
                int precision, ifci_stream_t stream);
 
+/* ifci_sigma_noalloc — the FP64 sigma = H c of ifci_sigma, for callers that
+ * cannot allocate device memory: a host program whose memory manager owns all
+ * of the GPU's memory (a caching allocator that reserved it up front), or a
+ * latency-bound caller that cannot accept cudaMalloc's implicit device
+ * synchronisation.  The paper has no counterpart; it exists for such callers.
+ * No handle: all scratch (folded integrals, the intermediates D and G, work
+ * lists) lives in one file-scope device array of ifci_sigma_noalloc_max_bytes()
+ * = 16 MiB, which every GPU that loads the library holds until the process
+ * exits.  The call makes no cudaMalloc/cudaFree and calls no allocating
+ * library routine.
+ *   Arguments and layout as for ifci_sigma (current CUDA device; FP64 only).
+ *   Returns INVALID_ARG, without launching anything, when the problem's
+ *   scratch (8*npair^2 + 16*npair*nstr^2 bytes plus small work lists) exceeds
+ *   the array; CUDA_ERR on a CUDA failure.
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call shares the array and each call overwrites what
+ * it reads, so nothing carries over between calls — but calls that overlap
+ * on the GPU (other streams, other host threads) race on the array. */
+size_t ifci_sigma_noalloc_max_bytes(void);
+int ifci_sigma_noalloc(const ifci_strings_t *str, const double *h1, const double *eri,
+                       const double *c, double *sigma, ifci_stream_t stream);
+
 /* ifci_hdiag — diagonal <I|H|I> of the same H (no constant), for the
  * Davidson preconditioner.  hd: device double[nstr*nstr].  Asynchronous. */
 int ifci_hdiag(ifci_handle_t handle, const ifci_strings_t *str,

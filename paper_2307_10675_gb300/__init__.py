@@ -8,5 +8,6 @@ from .api import (  # noqa: F401
     CIProblem, Handle, IfciError, StringTables, SystemArrays,
     body_subsets, davidson_opts,
     ifci_build_strings, ifci_davidson_batched, ifci_frozen_core, ifci_hdiag, ifci_increments,
-    ifci_num_subsets, ifci_rdm_backward, ifci_sigma, ifci_string_counts,
+    ifci_num_subsets, ifci_rdm_backward, ifci_sigma, ifci_sigma_noalloc, ifci_sigma_noalloc_max_bytes,
+    ifci_string_counts,
 )

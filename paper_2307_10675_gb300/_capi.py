@@ -27,6 +27,7 @@ EXPORTS = [
     "ifci_kernel_launches", "ifci_string_counts", "ifci_build_strings", "ifci_sigma", "ifci_hdiag",
     "ifci_frozen_core", "ifci_davidson_default_opts", "ifci_davidson_batched", "ifci_num_subsets",
     "ifci_increments", "ifci_rdm_backward", "ifci_profile_enable", "ifci_profile_read",
+    "ifci_sigma_noalloc", "ifci_sigma_noalloc_max_bytes",
 ]
 PROFILE_KINDS = {"gather": 0, "contract": 1, "scatter": 2, "vector": 3, "other": 4}
 
@@ -89,6 +90,9 @@ def load(build_if_missing: bool = True):
                                   c_double_p, c_double_p, c_double_p, c_int_p, c_int_p, c_void_p]
     L.ifci_rdm_backward.argtypes = [H, ctypes.POINTER(System), c_int, ctypes.POINTER(DavidsonOpts), c_double,
                                     c_void_p, c_void_p, c_int, c_void_p]
+    L.ifci_sigma_noalloc.argtypes = [ctypes.POINTER(Strings), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    L.ifci_sigma_noalloc_max_bytes.argtypes = []
+    L.ifci_sigma_noalloc_max_bytes.restype = c_size_t
     L.ifci_profile_enable.argtypes = [H, c_int]
     L.ifci_profile_read.argtypes = [H, c_int, c_double_p, ctypes.POINTER(c_ll)]
     _LIB = L

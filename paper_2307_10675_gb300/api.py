@@ -147,6 +147,18 @@ def ifci_sigma(handle: Handle, tables: StringTables, h1: torch.Tensor, eri: torc
     return sigma
 
 
+def ifci_sigma_noalloc(tables: StringTables, h1: torch.Tensor, eri: torch.Tensor, c: torch.Tensor,
+                       sigma: torch.Tensor, stream=None) -> int:
+    """FP64 sigma into a caller-provided ``sigma`` with no device allocation by
+    the library (fixed scratch array).  Returns the C status code."""
+    return int(_lib().ifci_sigma_noalloc(tables.as_c(), _ptr(h1), _ptr(eri), _ptr(c), _ptr(sigma),
+                                         _stream(stream)))
+
+
+def ifci_sigma_noalloc_max_bytes() -> int:
+    return int(_lib().ifci_sigma_noalloc_max_bytes())
+
+
 def ifci_hdiag(handle: Handle, tables: StringTables, h1: torch.Tensor, eri: torch.Tensor,
                hd: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     if hd is None:

@@ -214,3 +214,12 @@ extern "C" int ifci_hdiag(ifci_handle_t h, const ifci_strings_t *str, const doub
     // host vectors above are pageable: the copies complete before cudaMemcpyAsync returns
     return IFCI_OK;
 }
+
+namespace ifci {
+
+cudaError_t launch_fold_raw(const FoldDesc *d_desc, int max_np, cudaStream_t s) {
+    fold_kernel<<<1, 256, max_np * sizeof(double), s>>>(d_desc);
+    return cudaGetLastError();
+}
+
+}  // namespace ifci

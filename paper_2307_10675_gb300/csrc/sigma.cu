@@ -274,3 +274,21 @@ int launch_convert_w(ifci_handle_t h, int nprob, const SigmaProb *d_probs, cudaS
 }
 
 }  // namespace ifci
+
+namespace ifci {
+
+// Launches the FP64 gather, contraction and scatter of one prepared wave
+// without a handle (used by the allocation-free sigma entry point).
+cudaError_t launch_sigma_fp64_raw(const SigmaProb *d_probs, const WorkItem *d_items, int nitem,
+                                  const WorkItem *d_tiles, int ntile, double *D, double *G, cudaStream_t s) {
+    gather_kernel<double><<<nitem, kGatherChunk, 0, s>>>(d_probs, d_items, D);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    contract_simt_kernel<double><<<ntile, 256, 0, s>>>(d_probs, d_tiles, D, G);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    scatter_kernel<double><<<nitem, kGatherChunk, 0, s>>>(d_probs, d_items, G);
+    return cudaGetLastError();
+}
+
+}  // namespace ifci
