@@ -22,6 +22,7 @@ struct ifci_handle_s {
     size_t ws_top = 0;           // bump pointer
     std::string last_error;
     long long launches = 0;
+    int *d_err = nullptr;        // device flag set by kernels whose bounded waits ran out
     // vectors kept by ifci_increments for ifci_rdm_backward
     struct Kept {
         bool valid = false;

@@ -206,7 +206,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
     IFCI_TRY(dav_init(h, b, s));
 
     int *h_nactive = nullptr;
-    IFCI_CUDA_TRY(h, cudaMallocHost(&h_nactive, sizeof(int)));
+    IFCI_CUDA_TRY(h, cudaMallocHost(&h_nactive, 2 * sizeof(int)));
     int st = dav_iterate(h, b, hi, lo ? &lop : nullptr, d_hi, d_lo, D, G, h_nactive, s);
     cudaFreeHost(h_nactive);
     IFCI_TRY(st);

@@ -87,6 +87,7 @@ __global__ void init_kernel(const DavProb *__restrict__ probs, DavState *__restr
         s.status = IFCI_ERR_NOT_CONVERGED;
         s.tslot = -1;
         s.ref = bi[0] * p.nstr + bi[0];
+        s.force = 0;
         s.theta = bv[0];
         s.theta_prev = 1e300;
         s.rnorm = 1e300;
@@ -123,23 +124,33 @@ __global__ void select_kernel(const DavState *__restrict__ st, int nprob, int mi
 
 // ------------------------------------------------------------------ subspace
 
-// partial[item][j] = <b_j | sigma_new> over the item's determinants, j <= newest
+// partial[item][j] = <b_j | sigma_new> over the item's determinants, j <= newest.
+// Mixed mode: slot 0 holds the restart vector x whose sigma is FP64-exact, so
+// its entry is taken as <sigma(x) | b_new> (equal to <x | sigma(b_new)> for the
+// symmetric H) instead of through the low-precision sigma of b_new; otherwise
+// the integral rounding of the low-precision sigma would enter the projected
+// matrix at O(u |H|) however small the residual is.
 __global__ void __launch_bounds__(256) dots_kernel(const DavProb *__restrict__ probs, const DavState *__restrict__ st,
-                                                   const WorkItem *__restrict__ items, double *__restrict__ part) {
+                                                   const WorkItem *__restrict__ items, double *__restrict__ part,
+                                                   int mixed) {
     const WorkItem it = items[blockIdx.x];
     const DavState s = st[it.prob];
     if (!s.active) return;
     const DavProb &p = probs[it.prob];
     const int k = s.newest + 1;
+    const bool exact0 = mixed && s.newest > 0;
     double acc[kMaxSpace + 1];
 #pragma unroll
     for (int j = 0; j <= kMaxSpace; j++) acc[j] = 0.0;
     const double *Sn = p.S + (long long)s.newest * p.ndet;
+    const double *Bn = p.B + (long long)s.newest * p.ndet;
     long long end = min(it.start + (long long)kVecChunk, p.ndet);
     for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) {
         double sv = Sn[I];
+        if (exact0) acc[0] += p.S[I] * Bn[I];
+        else acc[0] += p.B[I] * sv;
 #pragma unroll
-        for (int j = 0; j <= kMaxSpace; j++)
+        for (int j = 1; j <= kMaxSpace; j++)
             if (j < k) acc[j] += p.B[(long long)j * p.ndet + I] * sv;
     }
     block_sum_store<kMaxSpace + 1>(acc, k, part + (long long)blockIdx.x * kNP);
@@ -307,7 +318,9 @@ __global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__rest
     s.rnorm = sqrt(sum[kMaxSpace + 1]);
     const double *y = ys + (long long)i * kNP;
     bool exact = !mixed || k == 1;
-    bool conv = exact && s.rnorm < r_tol && fabs(s.theta - s.theta_prev) < e_tol;
+    // mixed mode judges only FP64-exact residuals, so the residual alone decides
+    // (energy error ~ r^2 / gap); the FP64 path also asks for a settled energy
+    bool conv = exact && s.rnorm < r_tol && (mixed || fabs(s.theta - s.theta_prev) < e_tol);
     if (exact) s.theta_prev = s.theta;
     if (conv || s.rnorm == 0.0) {
         s.active = 0;
@@ -328,8 +341,13 @@ __global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__rest
     atomicAdd(nactive, 1);
     double *c = coef + (long long)i * kNP;
     double *Gm = gs + (long long)i * kMaxSpace * kMaxSpace;
-    if (k >= restart_at) {
+    // the spin-flip-even sector has nstr (nstr + 1) / 2 dimensions: a full
+    // subspace restarts (mixed mode) so that its final check is FP64-exact
+    const int nsym = p.nstr * (p.nstr + 1) / 2;
+    if (k >= restart_at || (mixed && (k >= nsym || s.force))) {
+        s.force = 0;
         s.restart = 1;
+        s.kold = k;
         if (mixed) {
             // basis becomes [x]; its FP64 sigma is built next iteration
             s.k = 1;
@@ -358,7 +376,7 @@ __global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__rest
 __global__ void __launch_bounds__(256) restart_kernel(const DavProb *__restrict__ probs,
                                                       const DavState *__restrict__ st,
                                                       const WorkItem *__restrict__ items, const double *__restrict__ ys,
-                                                      int max_space, int old_k, int mixed) {
+                                                      int max_space, int mixed) {
     const WorkItem it = items[blockIdx.x];
     const DavState s = st[it.prob];
     if (!s.active || !s.restart) return;
@@ -368,11 +386,12 @@ __global__ void __launch_bounds__(256) restart_kernel(const DavProb *__restrict_
     for (int j = 0; j < kMaxSpace; j++) y[j] = ys[(long long)it.prob * kNP + j];
     long long end = min(it.start + (long long)kVecChunk, p.ndet);
     const double *T = p.B + (long long)max_space * p.ndet;
+    const int kk = s.kold;   // only the slots of the old subspace are read
     for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) {
         double x = 0.0, sx = 0.0;
 #pragma unroll
         for (int j = 0; j < kMaxSpace; j++) {
-            if (j < old_k) {
+            if (j < kk) {
                 x += y[j] * p.B[(long long)j * p.ndet + I];
                 sx += y[j] * p.S[(long long)j * p.ndet + I];
             }
@@ -479,11 +498,19 @@ __global__ void __launch_bounds__(256) normalize_kernel(const DavProb *__restric
 }
 
 __global__ void advance_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st, int nprob,
-                               double r_tol) {
+                               double r_tol, int mixed) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nprob) return;
     DavState s = st[i];
     if (!s.active) return;
+    if (s.tslot >= 0 && s.tnorm2 < 1e-28 && mixed) {
+        // mixed mode: keep the subspace, rebuild sigma of the newest vector and
+        // restart at the next check, whose sigma of x is FP64-exact
+        s.force = 1;
+        s.restart = 0;
+        st[i] = s;
+        return;
+    }
     if (s.tslot >= 0 && s.tnorm2 < 1e-28) {
         // the correction vanished after orthogonalisation: the subspace is exhausted
         s.active = 0;
@@ -538,14 +565,14 @@ int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_
                 void *D, void *G, int *h_nactive, cudaStream_t s) {
     const int nitem = (int)b.vitems.size();
     const bool mixed = lo_plan != nullptr;
-    const int restart_at = mixed ? std::min(b.max_space, 4) : b.max_space;
+    const int restart_at = mixed ? std::min(b.max_space, 8) : b.max_space;
     for (int it = 0; it < b.max_iter + 2; it++) {
         select_kernel<<<(b.nprob + 127) / 128, 128, 0, s>>>(b.d_state, b.nprob, mixed ? 1 : 0, d_hi, d_lo);
         IFCI_LAUNCH_CHECK(h);
         IFCI_TRY(run_sigma(h, hi_plan, IFCI_FP64, D, G, s));
         if (mixed) IFCI_TRY(run_sigma(h, *lo_plan, b.precision, D, G, s));
         ProfScope vec_scope(h, s, PK_VECTOR);
-        dots_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);
+        dots_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part, mixed ? 1 : 0);
         IFCI_LAUNCH_CHECK(h);
         solve_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_gs, b.d_y);
         IFCI_LAUNCH_CHECK(h);
@@ -557,8 +584,7 @@ int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_
         check_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_coef, b.d_y, b.d_gs, b.max_space,
                                             restart_at, mixed ? 1 : 0, b.max_iter, b.e_tol, b.r_tol, b.d_nactive);
         IFCI_LAUNCH_CHECK(h);
-        restart_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, restart_at,
-                                             mixed ? 1 : 0);
+        restart_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, mixed ? 1 : 0);
         IFCI_LAUNCH_CHECK(h);
         for (int pass = 0; pass < 2; pass++) {
             ortho_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_coef, b.max_space, b.d_part);
@@ -568,11 +594,17 @@ int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_
         }
         normalize_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.max_space);
         IFCI_LAUNCH_CHECK(h);
-        advance_kernel<<<(b.nprob + 127) / 128, 128, 0, s>>>(b.d_probs, b.d_state, b.nprob, b.r_tol);
+        advance_kernel<<<(b.nprob + 127) / 128, 128, 0, s>>>(b.d_probs, b.d_state, b.nprob, b.r_tol,
+                                                             mixed ? 1 : 0);
         IFCI_LAUNCH_CHECK(h);
         if (h->prof) prof_end(h, s);
         IFCI_CUDA_TRY(h, cudaMemcpyAsync(h_nactive, b.d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(h_nactive + 1, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
         IFCI_CUDA_TRY(h, cudaStreamSynchronize(s));
+        if (h_nactive[1]) {
+            cudaMemsetAsync(h->d_err, 0, sizeof(int), s);
+            return set_error(h, IFCI_ERR_TIMEOUT, "davidson: a bounded device wait ran out");
+        }
         if (*h_nactive == 0) break;
     }
     ritz_out_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y);

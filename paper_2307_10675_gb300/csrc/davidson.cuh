@@ -25,6 +25,8 @@ struct DavState {
     int status;
     int tslot;               // slot holding the correction vector
     int ref;                 // index of the closed-shell starting determinant
+    int force;               // mixed mode: restart at the next check (subspace exhausted)
+    int kold;                // subspace size just before the last restart
     double theta, theta_prev, rnorm, tnorm2, energy;
 };
 

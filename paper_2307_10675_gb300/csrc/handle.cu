@@ -117,9 +117,16 @@ int ifci_handle_create(ifci_handle_t *handle, size_t workspace_bytes, int device
     cudaGetDevice(&prev);
     cudaSetDevice(device);
     int st = IFCI_OK;
-    if (workspace_bytes) st = ifci::ws_reserve(h, workspace_bytes);
+    if (cudaMalloc(&h->d_err, 256) != cudaSuccess || cudaMemset(h->d_err, 0, 256) != cudaSuccess) {
+        cudaGetLastError();
+        h->d_err = nullptr;
+        st = IFCI_ERR_CUDA;
+    }
+    if (st == IFCI_OK && workspace_bytes) st = ifci::ws_reserve(h, workspace_bytes);
     cudaSetDevice(prev);
     if (st != IFCI_OK) {
+        if (h->d_err) cudaFree(h->d_err);
+        if (h->ws) cudaFree(h->ws);
         delete h;
         return st;
     }
@@ -137,6 +144,7 @@ int ifci_handle_destroy(ifci_handle_t h) {
     for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
     if (h->ws) cudaFree(h->ws);
     if (h->kept.vec) cudaFree(h->kept.vec);
+    if (h->d_err) cudaFree(h->d_err);
     cudaSetDevice(prev);
     delete h;
     return IFCI_OK;

@@ -1,16 +1,320 @@
-// Tensor-core (tcgen05) contraction G = W D for the BF16 and TF32 paths.
+// Tensor-core (tcgen05) contraction G = W D for the BF16 path, with the
+// gather D = E+ c fused into the construction of the MMA's A operand.
+//
+// One tile = 128 determinants (the MMA's M, one TMEM lane each) x all npair
+// output pairs (N <= 256 columns of FP32 in TMEM) x all npair input pairs (K).
+//   A (M x K, K-major, SWIZZLE_128B) : D^T rows, built in shared memory by the
+//       128 threads, one determinant each, from the sorted alpha/beta
+//       excitation lists (no atomics, one rounding per element)
+//   B (N x K, K-major, SWIZZLE_128B) : the folded integrals W of the
+//       problem, a pre-swizzled BF16 image copied with one bulk async copy
+//       (cp.async.bulk) whenever the CTA moves to a new problem
+//   D (M x N, FP32, TMEM)            : G^T of the tile; the epilogue reads it
+//       with tcgen05.ld (one determinant per thread) and stores G[A][K] so
+//       that a warp writes 32 consecutive determinants per pair.
+// CTAs are persistent and take contiguous tile ranges, so W is reloaded only
+// at problem boundaries.  Every mbarrier wait is bounded; on a timeout the
+// kernel records an error flag, frees its TMEM and returns.
+#include <cuda_bf16.h>
+
 #include "sigma.cuh"
 
 namespace ifci {
 
-int tc_supported(int precision) { return 0; }
-int tc_operand_bytes(int np, int precision) { return 256; }
-int launch_tc_pack_w(ifci_handle_t h, int nprob, const SigmaProb *d_probs, int precision, cudaStream_t s) {
-    return set_error(h, IFCI_ERR_UNSUPPORTED, "tensor-core path not built");
+namespace {
+
+constexpr int kTM = 128;            // determinants per tile (MMA M)
+constexpr int kAtomBytes = 128;     // one swizzle atom row: 64 BF16
+constexpr int kTmemCols = 256;      // accumulator columns allocated per CTA
+constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
+
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+__host__ __device__ inline int k_atoms(int np) { return (np + 63) / 64; }
+__host__ __device__ inline int n_pad(int np) { return round_up(np, 16); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
+// tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row
+// groups 1024 B apart (SBO), version 1, base offset 0.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                           // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset
+    d |= (uint64_t)1 << 46;                           // descriptor version
+    d |= (uint64_t)2 << 61;                           // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, A and B K-major.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4)                      // D format FP32
+         | (1u << 7)                      // A format BF16
+         | (1u << 10)                     // B format BF16
+         | ((uint32_t)(N >> 3) << 17)
+         | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// Bounded wait on an mbarrier phase; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(double lo, double hi) {
+    __nv_bfloat16 a = __double2bfloat16(lo), b = __double2bfloat16(hi);
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+__global__ void __launch_bounds__(kTM, 1)
+tc_contract_bf16_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__ tiles, int ntile,
+                        size_t w_bytes_max, float *__restrict__ G, int *__restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bar_w, bar_mma;
+    __shared__ uint32_t tmem_slot;
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *Wsm = base;
+    uint8_t *Asm = base + ((w_bytes_max + 1023) & ~(size_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t bw = smem_u32(&bar_w), bm = smem_u32(&bar_mma);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(bw, 1);
+        mbar_init(bm, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    // contiguous tile range of this CTA
+    const int per = (ntile + gridDim.x - 1) / gridDim.x;
+    const int t0 = blockIdx.x * per, t1 = min(ntile, t0 + per);
+    int cur = -1;
+    uint32_t ph_w = 0, ph_m = 0;
+    bool ok = true;
+    for (int t = t0; t < t1 && ok; t++) {
+        const WorkItem tile = tiles[t];
+        const SigmaProb &p = probs[tile.prob];
+        if (p.active && !*p.active) continue;
+        const int np = p.np, N = n_pad(np), KA = k_atoms(np), KS = round_up(np, 16) / 16;
+        const long long ndet = p.ndet;
+        if (tile.prob != cur) {
+            if (tid == 0) bulk_load(smem_u32(Wsm), p.Wtc, (uint32_t)(KA * N * kAtomBytes), bw);
+            // block-wide vote so that every thread leaves the loop together
+            if (!__syncthreads_and(mbar_wait(bw, ph_w))) { ok = false; break; }
+            ph_w ^= 1;
+            cur = tile.prob;
+        }
+        // ---- fused gather: row tid of A = D^T of determinant K
+        const long long K = tile.start + tid;
+        {
+            const int nstr = p.nstr, nexc = p.nexc;
+            int ka = 0, kb = 0;
+            bool live = K < ndet;
+            if (live) {
+                ka = (int)(K / nstr);
+                kb = (int)(K % nstr);
+            }
+            const double *c = p.cbase + (p.cslot ? (long long)*p.cslot : 0ll) * p.stride;
+            const int32_t *ea = p.exc + (size_t)ka * nexc;
+            const int32_t *eb = p.exc + (size_t)kb * nexc;
+            int ia = 0, ib = 0;
+            int32_t xa = live ? ea[0] : 0, xb = live ? eb[0] : 0;
+            int pa = live ? exc_pair(xa) : -1, pb = live ? exc_pair(xb) : -1;
+            const double *crow = c + (long long)ka * nstr;
+            uint8_t *row = Asm + tid * kAtomBytes;
+            for (int ch = 0; ch < KA * 8; ch++) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int e = 0; e < 8; e += 2) {
+                    double v2[2];
+#pragma unroll
+                    for (int u = 0; u < 2; u++) {
+                        const int A = ch * 8 + e + u;
+                        double v = 0.0;
+                        if (pa == A) {
+                            v += exc_sign(xa) * c[(long long)exc_J(xa) * nstr + kb];
+                            if (++ia < nexc) { xa = ea[ia]; pa = exc_pair(xa); } else pa = -1;
+                        }
+                        if (pb == A) {
+                            v += exc_sign(xb) * crow[exc_J(xb)];
+                            if (++ib < nexc) { xb = eb[ib]; pb = exc_pair(xb); } else pb = -1;
+                        }
+                        v2[u] = v;
+                    }
+                    pk[e / 2] = pack_bf16x2(v2[0], v2[1]);
+                }
+                const int a = ch >> 3, cc = ch & 7;
+                uint4 *dst = (uint4 *)(row + a * (kTM * kAtomBytes) + ((cc ^ (tid & 7)) << 4));
+                *dst = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        // ---- MMA issue (one thread)
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t idesc = idesc_bf16(kTM, N);
+            const uint32_t a0 = smem_u32(Asm), b0 = smem_u32(Wsm);
+            for (int ks = 0; ks < KS; ks++) {
+                const uint32_t koff = (uint32_t)((ks & 3) * 32);   // 16 BF16 = 32 B inside the atom
+                const uint32_t aaddr = a0 + (uint32_t)(ks >> 2) * (kTM * kAtomBytes) + koff;
+                const uint32_t baddr = b0 + (uint32_t)(ks >> 2) * (uint32_t)(N * kAtomBytes) + koff;
+                mma_bf16(tmem, smem_desc(aaddr), smem_desc(baddr), idesc, ks > 0 ? 1u : 0u);
+            }
+            mma_commit(bm);
+        }
+        __syncwarp();
+        if (!__syncthreads_and(mbar_wait(bm, ph_m))) { ok = false; break; }
+        ph_m ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // ---- epilogue: TMEM -> G[A][K]
+        float *Gp = G + p.doff;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+            if (K < ndet) {
+#pragma unroll
+                for (int j = 0; j < 16; j++)
+                    if (c0 + j < np) Gp[(long long)(c0 + j) * ndet + K] = v[j];
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// BF16 image of W in the B-operand layout: [atom a][row n < N][128 B], the
+// 16-byte chunk c of row n stored at chunk c ^ (n % 8); zero padding.
+__global__ void pack_w_bf16_kernel(const SigmaProb *__restrict__ probs) {
+    const SigmaProb &p = probs[blockIdx.x];
+    const int np = p.np, N = n_pad(np), KA = k_atoms(np);
+    uint8_t *img = (uint8_t *)const_cast<void *>(p.Wtc);
+    for (int t = threadIdx.x; t < N * KA * 8; t += blockDim.x) {
+        const int n = t / (KA * 8), ch = t % (KA * 8);
+        uint32_t pk[4];
+        for (int e = 0; e < 8; e += 2) {
+            int k0 = ch * 8 + e, k1 = k0 + 1;
+            double v0 = (n < np && k0 < np) ? p.W[(long long)n * p.ld + k0] : 0.0;
+            double v1 = (n < np && k1 < np) ? p.W[(long long)n * p.ld + k1] : 0.0;
+            pk[e / 2] = pack_bf16x2(v0, v1);
+        }
+        const int a = ch >> 3, cc = ch & 7;
+        uint4 *dst = (uint4 *)(img + (size_t)a * N * kAtomBytes + (size_t)n * kAtomBytes + ((cc ^ (n & 7)) << 4));
+        *dst = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+}
+
+size_t tc_smem_bytes(int max_np) {
+    size_t w = (size_t)k_atoms(max_np) * n_pad(max_np) * kAtomBytes;
+    size_t a = (size_t)k_atoms(max_np) * kTM * kAtomBytes;
+    return 1024 + ((w + 1023) & ~(size_t)1023) + a;
+}
+
+}  // namespace
+
+int tc_supported(int precision) { return precision == IFCI_BF16 ? 1 : 0; }
+
+int tc_operand_bytes(int np, int precision) { return k_atoms(np) * n_pad(np) * kAtomBytes; }
+
+int launch_tc_pack_w(ifci_handle_t h, int nprob, const SigmaProb *d_probs, int precision, cudaStream_t s) {
+    if (precision != IFCI_BF16) return set_error(h, IFCI_ERR_UNSUPPORTED, "tensor-core precision %d", precision);
+    if (nprob <= 0) return IFCI_OK;
+    pack_w_bf16_kernel<<<nprob, 256, 0, s>>>(d_probs);
+    IFCI_LAUNCH_CHECK(h);
+    return IFCI_OK;
+}
+
 int launch_tc_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &w, int precision, const void *D,
                        void *G, cudaStream_t s) {
-    return set_error(h, IFCI_ERR_UNSUPPORTED, "tensor-core path not built");
+    (void)D;
+    if (precision != IFCI_BF16) return set_error(h, IFCI_ERR_UNSUPPORTED, "tensor-core precision %d", precision);
+    if (w.ntc == 0) return IFCI_OK;
+    int max_np = 0;
+    for (const SigmaProb &p : plan.probs) max_np = std::max(max_np, p.np);
+    if (max_np > 256) return set_error(h, IFCI_ERR_UNSUPPORTED, "tensor-core path: npair %d > 256", max_np);
+    if (!h->d_err) return set_error(h, IFCI_ERR_INVALID_ARG, "tensor-core path: no error flag");
+    // at least 116 KB of shared memory: one CTA per SM, so TMEM allocation never waits
+    const size_t smem = std::max(tc_smem_bytes(max_np), (size_t)116 * 1024);
+    const size_t wmax = (size_t)k_atoms(max_np) * n_pad(max_np) * kAtomBytes;
+    static int configured_smem = 0;
+    if ((int)smem > configured_smem) {
+        IFCI_CUDA_TRY(h, cudaFuncSetAttribute(tc_contract_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+        configured_smem = (int)smem;
+    }
+    const int grid = std::min(w.ntc, device_sm_count(h->device));
+    ProfScope ps(h, s, PK_CONTRACT);
+    tc_contract_bf16_kernel<<<grid, kTM, smem, s>>>(plan.d_probs, plan.d_tctiles + w.tc0, w.ntc, wmax, (float *)G,
+                                                    h->d_err);
+    IFCI_LAUNCH_CHECK(h);
+    return IFCI_OK;
 }
 
 }  // namespace ifci

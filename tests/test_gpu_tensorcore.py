@@ -1,0 +1,105 @@
+"""Tensor-core (tcgen05) BF16 sigma and the mixed-precision Davidson.
+
+Exactness test: with integrals and vectors on a coarse dyadic grid every
+operand of the contraction is exactly representable in BF16 and every
+partial sum in FP32, so the BF16 tensor-core sigma must equal the FP64 sigma
+to FP64 rounding.  This pins the operand layouts (swizzle, descriptors,
+instruction shape) exactly.  With random inputs the BF16 sigma differs from
+the oracle by the BF16 input rounding (unit roundoff u = 2^-8): the test
+bounds the relative norm error by 4u and the max error by 16u * max|sigma|.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import fci
+from synth import chain_24_uneven, random_ci_vector
+
+import paper_2307_10675_gb300 as ifci
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+U_BF16 = 2.0 ** -8
+
+
+@pytest.fixture(scope="module")
+def handle():
+    with ifci.Handle(0, 0) as h:
+        yield h
+
+
+def _dyadic_problem(n, seed):
+    rng = np.random.default_rng(seed)
+    npair = n * (n + 1) // 2
+    h1 = rng.integers(-2, 3, size=(n, n)) / 2.0
+    h1 = np.triu(h1) + np.triu(h1, 1).T
+    V = rng.integers(-2, 3, size=(npair, npair)) / 4.0
+    V = np.triu(V) + np.triu(V, 1).T
+    return torch.tensor(h1, device=DEV), torch.tensor(V, device=DEV)
+
+
+@pytest.mark.parametrize("n,m", [(6, 2), (10, 2), (14, 2), (18, 2), (8, 4)])
+def test_bf16_sigma_exact_on_dyadic_inputs(handle, n, m):
+    h1, V = _dyadic_problem(n, seed=n * 10 + m)
+    t = ifci.ifci_build_strings(handle, n, m)
+    rng = np.random.default_rng(n)
+    c = torch.tensor(rng.integers(-3, 4, size=t.nstr * t.nstr) / 4.0, device=DEV)
+    s64 = ifci.ifci_sigma(handle, t, h1, V, c, precision=ifci.IFCI_FP64)
+    s16 = ifci.ifci_sigma(handle, t, h1, V, c, precision=ifci.IFCI_BF16)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(s16.cpu().numpy(), s64.cpu().numpy(), rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("X", [(0,), (0, 1), (5, 7), (8, 11, 12), (2, 9, 16)])
+def test_bf16_sigma_against_oracle(handle, X):
+    chain = chain_24_uneven()
+    sysa = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=DEV),
+                             torch.tensor(chain.eri_packed(), device=DEV))
+    h1, eri, ecore = ifci.ifci_frozen_core(handle, sysa, X)
+    t = ifci.ifci_build_strings(handle, h1.shape[0], len(X))
+    c = torch.tensor(random_ci_vector(t.nstr, t.nstr, seed=4), device=DEV)
+    sig = ifci.ifci_sigma(handle, t, h1, eri, c, precision=ifci.IFCI_BF16)
+    torch.cuda.synchronize()
+    H = fci.Hamiltonian(fci.subsystem(chain, X))
+    cn = c.cpu().numpy().reshape(-1)
+    ref = H.matvec(cn) - ecore * cn
+    got = sig.cpu().numpy().reshape(-1)
+    err = got - ref
+    assert np.linalg.norm(err) <= 4 * U_BF16 * np.linalg.norm(ref)
+    assert np.max(np.abs(err)) <= 16 * U_BF16 * np.max(np.abs(ref))
+
+
+def test_bf16_sigma_full_size_matches_fp64_path(handle):
+    """CAS(6e,18o), 665,856 dets: BF16 tensor-core sigma vs the FP64 path (oracle-checked)."""
+    chain = chain_24_uneven()
+    X = tuple(b for b, s in enumerate(chain.body_sizes) if s == 6)[:3]
+    sysa = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=DEV),
+                             torch.tensor(chain.eri_packed(), device=DEV))
+    h1, eri, _ = ifci.ifci_frozen_core(handle, sysa, X)
+    t = ifci.ifci_build_strings(handle, 18, 3)
+    c = torch.tensor(random_ci_vector(816, 816, seed=8), device=DEV)
+    s64 = ifci.ifci_sigma(handle, t, h1, eri, c, precision=ifci.IFCI_FP64)
+    s16 = ifci.ifci_sigma(handle, t, h1, eri, c, precision=ifci.IFCI_BF16)
+    torch.cuda.synchronize()
+    err = (s16 - s64).cpu().numpy()
+    ref = s64.cpu().numpy()
+    assert np.linalg.norm(err) <= 4 * U_BF16 * np.linalg.norm(ref)
+
+
+def test_mixed_davidson_reaches_fp64_accuracy(handle):
+    """BF16 sigma for corrections, FP64 sigma for restart vectors: energies to 1e-8 Eh."""
+    chain = chain_24_uneven()
+    sysa = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=DEV),
+                             torch.tensor(chain.eri_packed(), device=DEV))
+    sets = [(0,), (3,), (0, 1), (5, 7), (8, 11, 12)]
+    probs = []
+    for X in sets:
+        h1, eri, ec = ifci.ifci_frozen_core(handle, sysa, X)
+        probs.append(ifci.CIProblem(h1.shape[0], len(X), h1, eri, ec))
+    e, it, st = ifci.ifci_davidson_batched(handle, probs, ifci.davidson_opts("bf16", r_tol=1e-7))
+    assert all(s == 0 for s in st)
+    for X, ei in zip(sets, e):
+        ref = fci.solve_subsystem(chain, X, tol=1e-10).energy
+        assert ei == pytest.approx(ref, abs=1e-8), X
