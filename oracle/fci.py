@@ -298,8 +298,25 @@ class CIResult:
     iterations: int = 0
 
 
-def solve_subsystem(system, X: Sequence[int], method: str = "auto", tol: float = 1e-9) -> CIResult:
-    """Lowest singlet CI energy E_X of body set X (core frozen, FCI in X's orbitals)."""
+def random_symmetric_start(nstr: int, seed: int) -> np.ndarray:
+    """Seeded N(0,1) vector projected on C = C^T: it overlaps every state of the
+    spin-flip-even sector (with probability one), unlike a single determinant,
+    which can be orthogonal to a charge-transfer ground state."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    C = rng.normal(size=(nstr, nstr))
+    return (0.5 * (C + C.T)).reshape(-1)
+
+
+def solve_subsystem(system, X: Sequence[int], method: str = "auto", tol: float = 1e-9,
+                    start: str = "random") -> CIResult:
+    """Lowest singlet CI energy E_X of body set X (core frozen, FCI in X's orbitals).
+
+    E_X is the lowest eigenvalue (Methods, definition of E_c(X)); the dense
+    path sees every root, the Lanczos path starts from a seeded random vector
+    of the singlet-containing sector (``start="reference"`` starts from the
+    reference determinant instead, which finds the lowest state only when
+    that state overlaps the reference).
+    """
     sub = subsystem(system, X)
     H = Hamiltonian(sub)
     if method == "auto":
@@ -307,9 +324,12 @@ def solve_subsystem(system, X: Sequence[int], method: str = "auto", tol: float =
     if method == "dense":
         e, c = lowest_singlet_dense(H)
         return CIResult(e, c, H.s_squared(c), H.ndet, "dense")
-    bonding_local = [sub.ncore + sub.active.index(system.bonding_orbital(b)) for b in sorted(X)]
-    v0 = np.zeros(H.ndet)
-    v0[H.reference_index(bonding_local)] = 1.0
+    if start == "reference":
+        bonding_local = [sub.ncore + sub.active.index(system.bonding_orbital(b)) for b in sorted(X)]
+        v0 = np.zeros(H.ndet)
+        v0[H.reference_index(bonding_local)] = 1.0
+    else:
+        v0 = random_symmetric_start(H.nstr, seed=1000003 * len(X) + sum(31 ** i * b for i, b in enumerate(sorted(X))))
     e, c, it = lanczos_lowest(H, v0, tol=tol, project=spin_flip_symmetrize(H.nstr))
     return CIResult(e, c, H.s_squared(c), H.ndet, "lanczos", it)
 

@@ -52,15 +52,23 @@ __device__ void block_sum_store(double (&v)[NV], int nv, double *out) {
 
 // ------------------------------------------------------------------ setup
 
-// Starting vector: the closed-shell determinant (I, I) of lowest diagonal.
+// Starting vector: the determinant of lowest diagonal H_II (with its mirror
+// image (I_b, I_a), to stay in the spin-flip-even sector) plus a small
+// deterministic pseudo-random symmetric component.  The random part gives the
+// start vector a nonzero overlap with every state of the sector: a single
+// determinant can be orthogonal to the lowest singlet (a charge-transfer
+// ground state), and the Davidson iteration would then converge to an
+// excited state.
+constexpr double kStartNoise = 0.1;   // norm of the random part before normalisation
+
 __global__ void init_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st) {
     const DavProb p = probs[blockIdx.x];
     __shared__ double bv[256];
-    __shared__ int bi[256];
+    __shared__ long long bi[256];
     double best = 1e300;
-    int besti = 0;
-    for (int i = threadIdx.x; i < p.nstr; i += blockDim.x) {
-        double v = p.hd[(long long)i * p.nstr + i];
+    long long besti = 0;
+    for (long long i = threadIdx.x; i < p.ndet; i += blockDim.x) {
+        double v = p.hd[i];
         if (v < best) { best = v; besti = i; }
     }
     bv[threadIdx.x] = best;
@@ -69,7 +77,7 @@ __global__ void init_kernel(const DavProb *__restrict__ probs, DavState *__restr
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
             double v2 = bv[threadIdx.x + o];
-            int i2 = bi[threadIdx.x + o];
+            long long i2 = bi[threadIdx.x + o];
             if (v2 < bv[threadIdx.x] || (v2 == bv[threadIdx.x] && i2 < bi[threadIdx.x])) {
                 bv[threadIdx.x] = v2;
                 bi[threadIdx.x] = i2;
@@ -86,7 +94,7 @@ __global__ void init_kernel(const DavProb *__restrict__ probs, DavState *__restr
         s.iters = 0;
         s.status = IFCI_ERR_NOT_CONVERGED;
         s.tslot = -1;
-        s.ref = bi[0] * p.nstr + bi[0];
+        s.ref = bi[0];
         s.force = 0;
         s.theta = bv[0];
         s.theta_prev = 1e300;
@@ -97,13 +105,59 @@ __global__ void init_kernel(const DavProb *__restrict__ probs, DavState *__restr
     }
 }
 
-__global__ void init_vec_kernel(const DavProb *__restrict__ probs, const DavState *__restrict__ st,
-                                const WorkItem *__restrict__ items) {
+// symmetric pseudo-random value in [-1, 1) of the unordered string pair {a, b}
+__device__ __forceinline__ double pair_noise(int a, int b) {
+    unsigned long long lo = (unsigned long long)min(a, b), hi = (unsigned long long)max(a, b);
+    unsigned long long x = (hi << 32) ^ lo ^ 0x9E3779B97F4A7C15ull;
+    x ^= x >> 30; x *= 0xBF58476D1CE4E5B9ull;
+    x ^= x >> 27; x *= 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// B_0 = e_ref (+ mirror) + kStartNoise * r / |r|_est ; partial |B_0|^2 per item
+__global__ void __launch_bounds__(256) init_vec_kernel(const DavProb *__restrict__ probs,
+                                                       const DavState *__restrict__ st,
+                                                       const WorkItem *__restrict__ items,
+                                                       double *__restrict__ part) {
     const WorkItem it = items[blockIdx.x];
     const DavProb &p = probs[it.prob];
-    const int ref = st[it.prob].ref;
+    const long long ref = st[it.prob].ref;
+    const int n = p.nstr;
+    const int ra = (int)(ref / n), rb = (int)(ref % n);
+    const long long refT = (long long)rb * n + ra;
+    const double w = ra == rb ? 1.0 : 0.7071067811865476;
+    const double amp = kStartNoise * sqrt(3.0 / (double)p.ndet);   // E|r|^2 = ndet / 3
+    double acc = 0.0;
     long long end = min(it.start + (long long)kVecChunk, p.ndet);
-    for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) p.B[I] = (I == ref) ? 1.0 : 0.0;
+    for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) {
+        const int a = (int)(I / n), b = (int)(I % n);
+        double v = amp * pair_noise(a, b);
+        if (I == ref || I == refT) v += w;
+        p.B[I] = v;
+        acc += v * v;
+    }
+    acc = warp_sum(acc);
+    __shared__ double red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < 8; i++) t += red[i];
+        part[(long long)blockIdx.x * kNP] = t;
+    }
+}
+
+__global__ void __launch_bounds__(256) init_scale_kernel(const DavProb *__restrict__ probs,
+                                                         const WorkItem *__restrict__ items,
+                                                         const double *__restrict__ part) {
+    const WorkItem it = items[blockIdx.x];
+    const DavProb &p = probs[it.prob];
+    double n2 = 0.0;
+    for (int w = 0; w < p.nitem; w++) n2 += part[(long long)(p.item0 + w) * kNP];
+    const double inv = 1.0 / sqrt(n2);
+    long long end = min(it.start + (long long)kVecChunk, p.ndet);
+    for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) p.B[I] *= inv;
 }
 
 // sigma selectors for the mixed mode: hi for the restart vector (k == 1), lo otherwise
@@ -556,7 +610,9 @@ __global__ void __launch_bounds__(256) ritz_out_kernel(const DavProb *__restrict
 int dav_init(ifci_handle_t h, DavBatch &b, cudaStream_t s) {
     init_kernel<<<b.nprob, 256, 0, s>>>(b.d_probs, b.d_state);
     IFCI_LAUNCH_CHECK(h);
-    init_vec_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems);
+    init_vec_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);
+    IFCI_LAUNCH_CHECK(h);
+    init_scale_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_vitems, b.d_part);
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;
 }

@@ -24,7 +24,7 @@ struct DavState {
     int iters;               // sigma builds so far
     int status;
     int tslot;               // slot holding the correction vector
-    int ref;                 // index of the closed-shell starting determinant
+    long long ref;           // index of the lowest-diagonal determinant (start vector)
     int force;               // mixed mode: restart at the next check (subspace exhausted)
     int kold;                // subspace size just before the last restart
     double theta, theta_prev, rnorm, tnorm2, energy;

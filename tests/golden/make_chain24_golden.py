@@ -2,8 +2,10 @@
 24-body uneven chain (seed 2308), used by the GPU parity tests.
 
 Calls only ``oracle/`` (and the seeded ``synth`` inputs).  Sample: every
-1-body set, 30 seeded 2-body sets plus the largest one, and 10 seeded 3-body
-sets with at most 30,000 determinants.  Run from the repository root:
+1-body set, 30 seeded 2-body sets plus the largest one, 10 seeded 3-body
+sets with at most 30,000 determinants, and two 3-body sets (132,496
+determinants each) whose lowest singlet is a charge-transfer state with
+almost no weight on the reference determinant.  Run from the repository root:
     python tests/golden/make_chain24_golden.py
 """
 import itertools
@@ -35,10 +37,11 @@ def main():
     triples = [X for X in itertools.combinations(range(24), 3)
                if math.comb(sum(sizes[b] for b in X), 3) ** 2 <= 30000]
     three = [triples[i] for i in sorted(rng.choice(len(triples), 10, replace=False))]
+    hard = [(5, 11, 15), (5, 14, 15)]
     out = {"system": "chain-24-uneven", "seed": s.seed, "body_sizes": sizes,
            "e0": fci.reference_energy(s), "energies": {}}
     t0 = time.time()
-    for X in ones + two + three:
+    for X in ones + two + three + hard:
         r = fci.solve_subsystem(s, X, tol=1e-10)
         out["energies"][",".join(map(str, X))] = {"energy": r.energy, "ndet": r.ndet, "s2": r.s2,
                                                    "method": r.method}

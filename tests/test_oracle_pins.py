@@ -180,6 +180,41 @@ def test_dense_and_lanczos_agree():
         assert abs(abs(rd.vector @ rl.vector) - 1.0) < 1e-8
 
 
+def test_lanczos_finds_a_charge_transfer_ground_state():
+    """Two bodies with no inter-body hopping: each body's electron count is
+    conserved, and the ground state lies in the charge-transfer sector (0, 4)
+    where the reference determinant (2, 2) has exactly zero weight.  The
+    random-start Lanczos must reach the dense lowest singlet; a reference
+    start stays in the (2, 2) sector above it."""
+    s = chain_4x2()
+    n = s.norb
+    h = np.zeros((n, n))
+    h[0, 0], h[1, 1] = -0.2, 2.0            # body 0: bonding high, antibonding far up
+    h[2, 2], h[3, 3] = -1.0, -0.9           # body 1: both orbitals low
+    h[4, 4], h[5, 5], h[6, 6], h[7, 7] = -1.0, 0.5, -1.0, 0.5
+    h[0, 1] = h[1, 0] = -0.1
+    h[2, 3] = h[3, 2] = -0.1
+    body = [0, 0, 1, 1, 2, 2, 3, 3]
+    V = np.zeros((s.npair, s.npair))
+    for p in range(n):
+        for q in range(p + 1):
+            for r in range(n):
+                for t in range(r + 1):
+                    A, B = pair_index(p, q), pair_index(r, t)
+                    if body[p] == body[q] and body[r] == body[t]:
+                        V[A, B] = 0.3 if (p == q and r == t) else 0.02
+    s2 = s.with_integrals(h, V)
+    dense = fci.solve_subsystem(s2, (0, 1), "dense")
+    lan = fci.solve_subsystem(s2, (0, 1), "lanczos", tol=1e-10)
+    ref = fci.solve_subsystem(s2, (0, 1), "lanczos", tol=1e-10, start="reference")
+    assert lan.energy == pytest.approx(dense.energy, abs=1e-10)
+    assert ref.energy > dense.energy + 0.1
+    sub = fci.subsystem(s2, (0, 1))
+    H = fci.Hamiltonian(sub)
+    bl = [sub.ncore + sub.active.index(s2.bonding_orbital(b)) for b in (0, 1)]
+    assert abs(dense.vector[H.reference_index(bl)]) < 1e-12
+
+
 def test_lowest_singlet_is_spin_flip_symmetric_and_lowest_overall():
     """C[Ia, Ib] = C[Ib, Ia] for the singlet (alpha-major string order), and for
     these seeds the lowest M_s = 0 root is that singlet."""
