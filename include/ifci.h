@@ -58,7 +58,11 @@ typedef enum {
     IFCI_FP64 = 0, /* every step in FP64 */
     IFCI_FP32 = 1, /* sigma contraction with FP32 inputs, FP32 accumulation */
     IFCI_TF32 = 2, /* sigma contraction on tensor cores, TF32 inputs, FP32 accumulation */
-    IFCI_BF16 = 3  /* sigma contraction on tensor cores, BF16 inputs, FP32 accumulation */
+    IFCI_BF16 = 3, /* sigma contraction on tensor cores, BF16 inputs, FP32 accumulation */
+    IFCI_FP64E = 4 /* sigma contraction to ~FP64 accuracy on BF16 tensor cores: both
+                      operands split into 5 slices of 8-bit integers, the 15 leading
+                      slice products accumulated exactly in FP32 per scale level,
+                      levels combined in FP64 (relative error ~2^-38 of max|W||D|) */
 } ifci_precision_t;
 
 typedef struct ifci_handle_s *ifci_handle_t;
@@ -197,6 +201,8 @@ typedef struct {
     double e_tol;        /* convergence: |E_k - E_{k-1}| < e_tol (default 1e-10 Eh) */
     double r_tol;        /* and ||H x - E x||_2 < r_tol (default 1e-6) */
     int refine;          /* non-FP64 precision: finish with FP64 sigma refinement (default 1) */
+    int hi_precision;    /* mixed mode: sigma of restart vectors, IFCI_FP64 or IFCI_FP64E
+                            (default IFCI_FP64E) */
     long long det_budget;/* determinants per sigma wave (0 = from workspace size) */
 } ifci_davidson_opts_t;
 

@@ -20,7 +20,7 @@ IFCI_ERR_NOT_CONVERGED = 4
 IFCI_ERR_TIMEOUT = 5
 IFCI_ERR_UNSUPPORTED = 6
 
-IFCI_FP64, IFCI_FP32, IFCI_TF32, IFCI_BF16 = 0, 1, 2, 3
+IFCI_FP64, IFCI_FP32, IFCI_TF32, IFCI_BF16, IFCI_FP64E = 0, 1, 2, 3, 4
 
 EXPORTS = [
     "ifci_handle_create", "ifci_handle_destroy", "ifci_last_error_string", "ifci_workspace_bytes",
@@ -49,7 +49,7 @@ class Problem(ctypes.Structure):
 
 class DavidsonOpts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("max_iter", c_int), ("max_space", c_int), ("e_tol", c_double),
-                ("r_tol", c_double), ("refine", c_int), ("det_budget", c_ll)]
+                ("r_tol", c_double), ("refine", c_int), ("hi_precision", c_int), ("det_budget", c_ll)]
 
 
 def lib_path() -> str:

@@ -15,10 +15,10 @@ import numpy as np
 import torch
 
 from . import _capi
-from ._capi import (IFCI_BF16, IFCI_ERR_NOT_CONVERGED, IFCI_FP32, IFCI_FP64, IFCI_OK,  # noqa: F401
+from ._capi import (IFCI_BF16, IFCI_ERR_NOT_CONVERGED, IFCI_FP32, IFCI_FP64, IFCI_FP64E, IFCI_OK,  # noqa: F401
                     IFCI_TF32)
 
-PRECISIONS = {"fp64": IFCI_FP64, "fp32": IFCI_FP32, "tf32": IFCI_TF32, "bf16": IFCI_BF16}
+PRECISIONS = {"fp64": IFCI_FP64, "fp32": IFCI_FP32, "tf32": IFCI_TF32, "bf16": IFCI_BF16, "fp64e": IFCI_FP64E}
 
 
 class IfciError(RuntimeError):
@@ -219,8 +219,10 @@ def ifci_frozen_core(handle: Handle, system: SystemArrays, bodies: Sequence[int]
 def davidson_opts(precision=IFCI_FP64, **kw) -> _capi.DavidsonOpts:
     o = _capi.DavidsonOpts()
     _lib().ifci_davidson_default_opts(ctypes.byref(o))
-    o.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     for k, v in kw.items():
+        if k == "hi_precision" and isinstance(v, str):
+            v = PRECISIONS[v]
         setattr(o, k, v)
     return o
 

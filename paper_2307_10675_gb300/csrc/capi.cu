@@ -22,9 +22,10 @@ int ifci_sigma(ifci_handle_t h, const ifci_strings_t *str, const double *h1, con
         return set_error(h, IFCI_ERR_INVALID_ARG, "ifci_sigma: inconsistent string table (norb=%d nelec=%d)",
                          str->norb, str->nelec_spin);
     if (c == sigma) return set_error(h, IFCI_ERR_INVALID_ARG, "ifci_sigma: sigma aliases c");
-    if (precision < IFCI_FP64 || precision > IFCI_BF16)
+    if (precision < IFCI_FP64 || precision > IFCI_FP64E)
         return set_error(h, IFCI_ERR_INVALID_ARG, "ifci_sigma: precision %d", precision);
     const bool tc = precision == IFCI_BF16 || precision == IFCI_TF32;
+    const bool oz = precision == IFCI_FP64E;
     if (tc && !tc_supported(precision))
         return set_error(h, IFCI_ERR_UNSUPPORTED, "ifci_sigma: precision %d not built", precision);
     IFCI_CUDA_TRY(h, cudaSetDevice(h->device));
@@ -41,22 +42,31 @@ int ifci_sigma(ifci_handle_t h, const ifci_strings_t *str, const double *h1, con
     IFCI_TRY(plan_sigma(h, plan, (long long)np * ndet, precision));
     const size_t eb = sigma_elem_bytes(precision);
     size_t need = ws_round(sizeof(FoldDesc)) + ws_round((size_t)ld * ld * 8) + ws_round((size_t)ld * ld * 4) +
-                  (tc ? ws_round((size_t)tc_operand_bytes(np, precision)) : 0) + plan_device_bytes(plan) +
+                  (tc ? ws_round((size_t)tc_operand_bytes(np, precision)) : 0) +
+                  (oz ? ws_round((size_t)oz_operand_bytes(np)) + ws_round(8) : 0) + plan_device_bytes(plan) +
                   2 * ws_round((size_t)plan.max_delems * eb);
     IFCI_TRY(ws_reserve(h, need));
     auto *fd = ws_take<FoldDesc>(h, 1);
     double *W = ws_take<double>(h, (size_t)ld * ld);
     float *Wf = ws_take<float>(h, (size_t)ld * ld);
     void *Wtc = tc ? (void *)ws_take<char>(h, tc_operand_bytes(np, precision)) : nullptr;
+    char *Woz = oz ? ws_take<char>(h, oz_operand_bytes(np)) : nullptr;
     plan.probs[0].W = W;
     plan.probs[0].Wf = Wf;
     plan.probs[0].Wtc = Wtc;
+    plan.probs[0].Woz = Woz;
+    plan.probs[0].Wexp = oz ? (double *)(Woz + (oz_operand_bytes(np) - np * 8 - 256)) : nullptr;
+    plan.probs[0].dscale = 2.0;
     FoldDesc f{n, 2 * str->nelec_spin, ld, h1, eri, W};
     IFCI_CUDA_TRY(h, cudaMemcpyAsync(fd, &f, sizeof(f), cudaMemcpyHostToDevice, s));
     IFCI_TRY(launch_fold(h, 1, fd, np, s));
     IFCI_TRY(upload_plan(h, plan, s));
     if (precision == IFCI_FP32) IFCI_TRY(launch_convert_w(h, 1, plan.d_probs, s));
     if (tc) IFCI_TRY(launch_tc_pack_w(h, 1, plan.d_probs, precision, s));
+    if (oz) {
+        IFCI_TRY(launch_oz_pack_w(h, 1, plan.d_probs, s));
+        IFCI_TRY(launch_oz_dscale(h, plan.d_probs, c, ndet, s));
+    }
     void *D = ws_take<char>(h, (size_t)plan.max_delems * eb);
     void *G = ws_take<char>(h, (size_t)plan.max_delems * eb);
     if (!D || !G) return set_error(h, IFCI_ERR_OOM, "ifci_sigma: workspace");

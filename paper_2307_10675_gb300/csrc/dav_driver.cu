@@ -14,8 +14,9 @@ static void dav_layout(const std::vector<ProbSpec> &specs, const ifci_davidson_o
     z = DavSizes{};
     std::map<std::pair<int, int>, int> cls;
     const int ms = o.max_space;
-    const bool lo = o.precision != IFCI_FP64;
+    const bool lo = o.precision == IFCI_FP32 || o.precision == IFCI_TF32 || o.precision == IFCI_BF16;
     const bool tc = o.precision == IFCI_BF16 || o.precision == IFCI_TF32;
+    const bool oz = hi_precision_of(o) == IFCI_FP64E;
     const size_t eb_lo = sigma_elem_bytes(o.precision);
     for (const ProbSpec &p : specs) {
         int nstr = (int)binom(p.n, p.m), nexc = p.m * (p.n - p.m + 1);
@@ -28,13 +29,15 @@ static void dav_layout(const std::vector<ProbSpec> &specs, const ifci_davidson_o
         z.bytes += ws_round((size_t)np * np * 8);                       // W
         if (lo) z.bytes += ws_round((size_t)np * np * 4);               // Wf
         if (tc) z.bytes += ws_round((size_t)tc_operand_bytes(np, o.precision));
+        if (oz) z.bytes += ws_round((size_t)oz_operand_bytes(np));
         z.bytes += ws_round((size_t)ndet * 8);                          // hd
         z.bytes += 2 * ws_round((size_t)(ms + 1) * ndet * 8);           // B, S
         z.nitem += (int)((ndet + kVecChunk - 1) / kVecChunk);
         z.max_pd = std::max(z.max_pd, (long long)np * ndet);
         z.sum_pd += (long long)np * ndet;
         z.n_items_sigma += (ndet + kGatherChunk - 1) / kGatherChunk;
-        z.n_tiles_sigma += ((np + kGemmTM - 1) / kGemmTM) * ((ndet + kGemmTN - 1) / kGemmTN) + (ndet + 127) / 128;
+        z.n_tiles_sigma += ((np + kGemmTM - 1) / kGemmTM) * ((ndet + kGemmTN - 1) / kGemmTN) +
+                           ((ndet + 127) / 128) * ((np + oz_tile_n() - 1) / oz_tile_n());
     }
     size_t n = specs.size();
     z.nclass = (int)cls.size();
@@ -62,8 +65,16 @@ size_t dav_workspace_bytes(const std::vector<ProbSpec> &specs, const ifci_davids
     return z.bytes;
 }
 
+int hi_precision_of(const ifci_davidson_opts_t &o) {
+    if (o.precision == IFCI_FP64) return IFCI_FP64;
+    if (o.precision == IFCI_FP64E) return IFCI_FP64E;
+    return o.hi_precision;
+}
+
 int check_opts(ifci_handle_t h, const ifci_davidson_opts_t &o) {
-    if (o.precision < IFCI_FP64 || o.precision > IFCI_BF16)
+    if (o.hi_precision != IFCI_FP64 && o.hi_precision != IFCI_FP64E)
+        return set_error(h, IFCI_ERR_INVALID_ARG, "davidson: hi_precision %d", o.hi_precision);
+    if (o.precision < IFCI_FP64 || o.precision > IFCI_FP64E)
         return set_error(h, IFCI_ERR_INVALID_ARG, "davidson: precision %d", o.precision);
     if ((o.precision == IFCI_BF16 || o.precision == IFCI_TF32) && !tc_supported(o.precision))
         return set_error(h, IFCI_ERR_UNSUPPORTED, "davidson: precision %d not built", o.precision);
@@ -81,8 +92,10 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
     IFCI_TRY(check_opts(h, o));
     DavSizes z;
     dav_layout(specs, o, z);
-    const bool lo = o.precision != IFCI_FP64;
+    const bool lo = o.precision == IFCI_FP32 || o.precision == IFCI_TF32 || o.precision == IFCI_BF16;
     const bool tc = o.precision == IFCI_BF16 || o.precision == IFCI_TF32;
+    const int hi_prec = hi_precision_of(o);
+    const bool oz = hi_prec == IFCI_FP64E;
     const int ms = o.max_space;
 
     // string tables per class
@@ -104,6 +117,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
     b.nprob = n;
     b.max_space = ms;
     b.precision = o.precision;
+    b.hi_precision = hi_prec;
     b.max_iter = o.max_iter;
     b.e_tol = o.e_tol;
     b.r_tol = o.r_tol;
@@ -121,10 +135,11 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
         double *W = ws_take<double>(h, (size_t)np * np);
         float *Wf = lo ? ws_take<float>(h, (size_t)np * np) : nullptr;
         void *Wtc = tc ? (void *)ws_take<char>(h, tc_operand_bytes(np, o.precision)) : nullptr;
+        char *Woz = oz ? ws_take<char>(h, oz_operand_bytes(np)) : nullptr;
         double *hd = ws_take<double>(h, ndet);
         double *B = ws_take<double>(h, (size_t)(ms + 1) * ndet);
         double *S = ws_take<double>(h, (size_t)(ms + 1) * ndet);
-        if (!W || !hd || !B || !S || (lo && !Wf) || (tc && !Wtc))
+        if (!W || !hd || !B || !S || (lo && !Wf) || (tc && !Wtc) || (oz && !Woz))
             return set_error(h, IFCI_ERR_OOM, "davidson: workspace (problem %d)", i);
         folds[i] = FoldDesc{p.n, 2 * p.m, np, p.h1, p.eri, W};
         hds[i] = HdiagDesc{p.n, nstr, tb.first, p.h1, p.eri, hd};
@@ -148,6 +163,9 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
         sp.n = p.n; sp.nstr = nstr; sp.nexc = nexc; sp.np = np; sp.ld = np;
         sp.ndet = ndet; sp.stride = ndet; sp.exc = tb.second;
         sp.W = W; sp.Wf = Wf; sp.Wtc = Wtc;
+        sp.Woz = Woz;
+        sp.Wexp = oz ? (double *)(Woz + (oz_operand_bytes(np) - np * 8 - 256)) : nullptr;
+        sp.dscale = 2.0;   // basis vectors are normalised: |D| <= 2
         sp.cbase = B; sp.sbase = S;
         hi.probs.push_back(sp);
         lop.probs.push_back(sp);
@@ -179,7 +197,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
         lop.probs[i].sslot = &b.d_state[i].newest;
         lop.probs[i].active = d_lo + i;
     }
-    IFCI_TRY(plan_sigma(h, hi, z.budget, IFCI_FP64));
+    IFCI_TRY(plan_sigma(h, hi, z.budget, hi_prec));
     if (lo) {
         long long budget_lo = z.budget * 8 / (long long)sigma_elem_bytes(o.precision);
         IFCI_TRY(plan_sigma(h, lop, budget_lo, o.precision));
@@ -202,6 +220,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
     IFCI_TRY(launch_fold(h, n, d_fold, maxnp, s));
     if (lo) IFCI_TRY(launch_convert_w(h, n, lop.d_probs, s));
     if (tc) IFCI_TRY(launch_tc_pack_w(h, n, lop.d_probs, o.precision, s));
+    if (oz) IFCI_TRY(launch_oz_pack_w(h, n, hi.d_probs, s));
     IFCI_TRY(launch_hdiag(h, d_hd, d_hwp, d_hws, (int)hw_prob.size(), kVecChunk, s));
     IFCI_TRY(dav_init(h, b, s));
 
@@ -236,6 +255,7 @@ void ifci_davidson_default_opts(ifci_davidson_opts_t *o) {
     o->e_tol = 1e-10;
     o->r_tol = 1e-6;
     o->refine = 1;
+    o->hi_precision = IFCI_FP64E;
     o->det_budget = 0;
 }
 

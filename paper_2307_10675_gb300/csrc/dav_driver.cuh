@@ -20,6 +20,7 @@ struct DavSizes {
 };
 
 int check_opts(ifci_handle_t h, const ifci_davidson_opts_t &o);
+int hi_precision_of(const ifci_davidson_opts_t &o);   // precision of the exact (restart) sigma
 // Upper bound of the workspace dav_solve takes (with ws_take) for these problems.
 size_t dav_workspace_bytes(const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o);
 // Solves every problem; carves its memory from the handle workspace after

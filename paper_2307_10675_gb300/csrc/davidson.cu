@@ -625,7 +625,7 @@ int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_
     for (int it = 0; it < b.max_iter + 2; it++) {
         select_kernel<<<(b.nprob + 127) / 128, 128, 0, s>>>(b.d_state, b.nprob, mixed ? 1 : 0, d_hi, d_lo);
         IFCI_LAUNCH_CHECK(h);
-        IFCI_TRY(run_sigma(h, hi_plan, IFCI_FP64, D, G, s));
+        IFCI_TRY(run_sigma(h, hi_plan, b.hi_precision, D, G, s));
         if (mixed) IFCI_TRY(run_sigma(h, *lo_plan, b.precision, D, G, s));
         ProfScope vec_scope(h, s, PK_VECTOR);
         dots_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part, mixed ? 1 : 0);

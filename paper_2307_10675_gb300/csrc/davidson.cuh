@@ -37,6 +37,7 @@ constexpr int kNP = kMaxSpace + 2;
 struct DavBatch {
     int nprob = 0, max_space = 12;
     int precision = IFCI_FP64;
+    int hi_precision = IFCI_FP64;
     int max_iter = 100;
     double e_tol = 1e-10, r_tol = 1e-6;
     std::vector<DavProb> probs;

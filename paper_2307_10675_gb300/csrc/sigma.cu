@@ -14,7 +14,7 @@
 
 namespace ifci {
 
-size_t sigma_elem_bytes(int precision) { return precision == IFCI_FP64 ? 8 : 4; }
+size_t sigma_elem_bytes(int precision) { return (precision == IFCI_FP64 || precision == IFCI_FP64E) ? 8 : 4; }
 
 template <typename TD>
 __global__ void __launch_bounds__(kGatherChunk)
@@ -171,6 +171,13 @@ int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision
                 plan.tctiles.push_back(WorkItem{(int)i, 0, s0});
                 w.ntc++;
             }
+        } else if (precision == IFCI_FP64E) {
+            // one tile = 128 determinants x oz_tile_n() output pairs (see sigma_oz.cu)
+            for (long long s0 = 0; s0 < p.ndet; s0 += 128)
+                for (int n0 = 0; n0 < p.np; n0 += oz_tile_n()) {
+                    plan.tctiles.push_back(WorkItem{(int)i, n0, s0});
+                    w.ntc++;
+                }
         } else {
             for (int m0 = 0; m0 < p.np; m0 += kGemmTM)
                 for (long long s0 = 0; s0 < p.ndet; s0 += kGemmTN) {
@@ -248,6 +255,12 @@ int run_sigma(ifci_handle_t h, const SigmaPlan &plan, int precision, void *D, vo
             ProfScope ps(h, s, PK_SCATTER);
             scatter_kernel<float><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
                                                                    (const float *)G);
+            IFCI_LAUNCH_CHECK(h);
+        } else if (precision == IFCI_FP64E) {
+            IFCI_TRY(launch_oz_contract(h, plan, w, G, s));
+            ProfScope ps(h, s, PK_SCATTER);
+            scatter_kernel<double><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
+                                                                    (const double *)G);
             IFCI_LAUNCH_CHECK(h);
         } else {
             IFCI_TRY(launch_tc_contract(h, plan, w, precision, D, G, s));

@@ -16,7 +16,10 @@ struct SigmaProb {
     const int32_t *exc;      // [nstr * nexc] excitation table of (n, nelec_spin)
     const double *W;         // [ld * ld] folded contraction matrix, FP64
     const float *Wf;         // [ld * ld] FP32 copy (FP32 path) or nullptr
-    const void *Wtc;         // tensor-core operand image (BF16/TF32 paths) or nullptr
+    const void *Wtc;         // tensor-core operand image (BF16 path) or nullptr
+    const void *Woz;         // sliced operand image of the FP64-emulating path or nullptr
+    double *Wexp;            // [np] power-of-two row scales of Woz
+    double dscale;           // power of two >= max |D| (FP64-emulating path)
     const double *cbase;
     double *sbase;
     const int *cslot;        // device slot index or nullptr (= 0)
@@ -61,6 +64,13 @@ int upload_plan(ifci_handle_t h, SigmaPlan &plan, cudaStream_t s);
 // elements of the precision's storage type (8 B for FP64, 4 B otherwise).
 int run_sigma(ifci_handle_t h, const SigmaPlan &plan, int precision, void *D, void *G, cudaStream_t s);
 size_t sigma_elem_bytes(int precision);
+
+// FP64-accurate contraction on BF16 tensor cores (sigma_oz.cu)
+int oz_operand_bytes(int np);                  // bytes of one problem's sliced W image (+ row scales)
+int oz_tile_n();                               // output pairs per tile
+int launch_oz_pack_w(ifci_handle_t h, int nprob, const SigmaProb *d_probs, cudaStream_t s);
+int launch_oz_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &w, void *G, cudaStream_t s);
+int launch_oz_dscale(ifci_handle_t h, SigmaProb *d_prob, const double *c, long long n, cudaStream_t s);
 
 // tensor-core contraction (sigma_tc.cu)
 int tc_supported(int precision);

@@ -88,8 +88,44 @@ def test_bf16_sigma_full_size_matches_fp64_path(handle):
     assert np.linalg.norm(err) <= 4 * U_BF16 * np.linalg.norm(ref)
 
 
-def test_mixed_davidson_reaches_fp64_accuracy(handle):
-    """BF16 sigma for corrections, FP64 sigma for restart vectors: energies to 1e-8 Eh."""
+# ---------------------------------------------------------------- FP64-accurate tensor-core contraction
+
+@pytest.mark.parametrize("n,m", [(6, 2), (14, 2), (18, 2), (8, 4)])
+def test_fp64e_sigma_exact_on_dyadic_inputs(handle, n, m):
+    h1, V = _dyadic_problem(n, seed=n * 10 + m + 1)
+    t = ifci.ifci_build_strings(handle, n, m)
+    rng = np.random.default_rng(n + 1)
+    c = torch.tensor(rng.integers(-3, 4, size=t.nstr * t.nstr) / 4.0, device=DEV)
+    s64 = ifci.ifci_sigma(handle, t, h1, V, c, precision=ifci.IFCI_FP64)
+    s64e = ifci.ifci_sigma(handle, t, h1, V, c, precision=ifci.IFCI_FP64E)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(s64e.cpu().numpy(), s64.cpu().numpy(), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("X", [(0,), (0, 1), (5, 7), (8, 11, 12), (2, 9, 16), "six"])
+def test_fp64e_sigma_matches_fp64(handle, X):
+    """Slice truncation: five 8-bit slices leave 2^-40 of each operand's scale and
+    the dropped slice products are of the same order, so one element of G is off
+    by at most about npair * 2^-39 max|W| max|D| (3e-10 relative at npair = 171).
+    The test asks for 1e-10 relative in norm and 1e-9 of max|sigma| per element."""
+    chain = chain_24_uneven()
+    if X == "six":
+        X = tuple(b for b, s in enumerate(chain.body_sizes) if s == 6)[:3]
+    sysa = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=DEV),
+                             torch.tensor(chain.eri_packed(), device=DEV))
+    h1, eri, _ = ifci.ifci_frozen_core(handle, sysa, X)
+    t = ifci.ifci_build_strings(handle, h1.shape[0], len(X))
+    c = torch.tensor(random_ci_vector(t.nstr, t.nstr, seed=12), device=DEV)
+    s64 = ifci.ifci_sigma(handle, t, h1, eri, c, precision=ifci.IFCI_FP64)
+    s64e = ifci.ifci_sigma(handle, t, h1, eri, c, precision=ifci.IFCI_FP64E)
+    torch.cuda.synchronize()
+    a, b = s64e.cpu().numpy().reshape(-1), s64.cpu().numpy().reshape(-1)
+    assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)
+    assert np.max(np.abs(a - b)) <= 1e-9 * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("prec,hi", [("fp64e", "fp64e"), ("bf16", "fp64e"), ("bf16", "fp64")])
+def test_tensor_core_davidson_reaches_fp64_accuracy(handle, prec, hi):
     chain = chain_24_uneven()
     sysa = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=DEV),
                              torch.tensor(chain.eri_packed(), device=DEV))
@@ -98,7 +134,7 @@ def test_mixed_davidson_reaches_fp64_accuracy(handle):
     for X in sets:
         h1, eri, ec = ifci.ifci_frozen_core(handle, sysa, X)
         probs.append(ifci.CIProblem(h1.shape[0], len(X), h1, eri, ec))
-    e, it, st = ifci.ifci_davidson_batched(handle, probs, ifci.davidson_opts("bf16", r_tol=1e-7))
+    e, it, st = ifci.ifci_davidson_batched(handle, probs, ifci.davidson_opts(prec, hi_precision=hi, r_tol=1e-7))
     assert all(s == 0 for s in st)
     for X, ei in zip(sets, e):
         ref = fci.solve_subsystem(chain, X, tol=1e-10).energy
