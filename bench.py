@@ -36,7 +36,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16", "fp64e"])
     ap.add_argument("--max-order", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -274,7 +274,7 @@ def main():
         dtype = "f64"
     else:
         bf = peaks.get("bf16_tflops_sustained", 1700.0)
-        ratio = {"bf16": 1.0, "tf32": 0.5, "fp32": 1.0 / 28.0}[args.precision]
+        ratio = {"bf16": 1.0, "fp64e": 1.0, "tf32": 0.5, "fp32": 1.0 / 28.0}[args.precision]
         pk = bf * ratio
         roof = {"bound": "tensor", "achieved": achieved_tf, "peak": pk, "unit": "TFLOP/s",
                 "frac": (achieved_tf / pk) if achieved_tf else None, "traffic": None,

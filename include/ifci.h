@@ -85,8 +85,9 @@ long long ifci_kernel_launches(ifci_handle_t handle);
 /* Per-kernel-class timing with CUDA events recorded on the launching stream
  * around every kernel the library issues (no paper counterpart; it serves
  * the roofline measurement).  enable != 0 turns it on and zeroes the totals.
- * Classes: 0 sigma gather, 1 sigma contraction, 2 sigma scatter,
- * 3 Davidson vector kernels, 4 other.  ifci_profile_read synchronises the
+ * Classes: 0 sigma gather (and quantisation), 1 sigma contraction (FP64,
+ * FP32, BF16), 2 sigma scatter, 3 Davidson vector kernels, 4 other,
+ * 5 FP64-emulating tensor-core contraction.  ifci_profile_read synchronises the
  * recorded events and returns the accumulated milliseconds and launches. */
 int ifci_profile_enable(ifci_handle_t handle, int enable);
 int ifci_profile_read(ifci_handle_t handle, int kind, double *ms, long long *launches);

@@ -29,7 +29,7 @@ EXPORTS = [
     "ifci_increments", "ifci_rdm_backward", "ifci_profile_enable", "ifci_profile_read",
     "ifci_sigma_noalloc", "ifci_sigma_noalloc_max_bytes",
 ]
-PROFILE_KINDS = {"gather": 0, "contract": 1, "scatter": 2, "vector": 3, "other": 4}
+PROFILE_KINDS = {"gather": 0, "contract": 1, "scatter": 2, "vector": 3, "other": 4, "contract_hi": 5}
 
 
 class Strings(ctypes.Structure):

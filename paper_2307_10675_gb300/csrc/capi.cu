@@ -43,7 +43,8 @@ int ifci_sigma(ifci_handle_t h, const ifci_strings_t *str, const double *h1, con
     const size_t eb = sigma_elem_bytes(precision);
     size_t need = ws_round(sizeof(FoldDesc)) + ws_round((size_t)ld * ld * 8) + ws_round((size_t)ld * ld * 4) +
                   (tc ? ws_round((size_t)tc_operand_bytes(np, precision)) : 0) +
-                  (oz ? ws_round((size_t)oz_operand_bytes(np)) + ws_round(8) : 0) + plan_device_bytes(plan) +
+                  (oz ? ws_round((size_t)oz_operand_bytes(np)) + ws_round(8) : 0) +
+                  ((tc || oz) ? ws_round((size_t)nstr * kBlk16Stride) : 0) + plan_device_bytes(plan) +
                   2 * ws_round((size_t)plan.max_delems * eb);
     IFCI_TRY(ws_reserve(h, need));
     auto *fd = ws_take<FoldDesc>(h, 1);
@@ -57,9 +58,12 @@ int ifci_sigma(ifci_handle_t h, const ifci_strings_t *str, const double *h1, con
     plan.probs[0].Woz = Woz;
     plan.probs[0].Wexp = oz ? (double *)(Woz + (oz_operand_bytes(np) - np * 8 - 256)) : nullptr;
     plan.probs[0].dscale = 2.0;
+    uint8_t *blk = (tc || oz) ? ws_take<uint8_t>(h, (size_t)nstr * kBlk16Stride) : nullptr;
+    plan.probs[0].blk = blk;
     FoldDesc f{n, 2 * str->nelec_spin, ld, h1, eri, W};
     IFCI_CUDA_TRY(h, cudaMemcpyAsync(fd, &f, sizeof(f), cudaMemcpyHostToDevice, s));
     IFCI_TRY(launch_fold(h, 1, fd, np, s));
+    if (blk) IFCI_TRY(launch_exc_blocks(h, nstr, nexc, str->exc, blk, s));
     IFCI_TRY(upload_plan(h, plan, s));
     if (precision == IFCI_FP32) IFCI_TRY(launch_convert_w(h, 1, plan.d_probs, s));
     if (tc) IFCI_TRY(launch_tc_pack_w(h, 1, plan.d_probs, precision, s));

@@ -38,6 +38,8 @@ struct ifci_handle_s {
 namespace ifci {
 
 constexpr int kPairBits = 9;       // pair index < 512  => norb <= 31
+constexpr int kBlk16 = 16;         // 16-pair blocks of the tensor-core paths (npair <= 256)
+constexpr int kBlk16Stride = 20;   // bytes per string in the block-offset table
 constexpr int kMaxNorb = 31;
 constexpr int kMaxStr = 1 << 22;
 
@@ -78,7 +80,7 @@ int set_error(ifci_handle_t h, int code, const char *fmt, ...);
     } while (0)
 
 // profiling ---------------------------------------------------------------
-enum ProfKind { PK_GATHER = 0, PK_CONTRACT = 1, PK_SCATTER = 2, PK_VECTOR = 3, PK_OTHER = 4 };
+enum ProfKind { PK_GATHER = 0, PK_CONTRACT = 1, PK_SCATTER = 2, PK_VECTOR = 3, PK_OTHER = 4, PK_CONTRACT_HI = 5 };
 void prof_begin(ifci_handle_t h, cudaStream_t s, int kind);
 void prof_end(ifci_handle_t h, cudaStream_t s);
 void prof_collect(ifci_handle_t h);   // adds finished event pairs to the totals (synchronises them)
@@ -112,5 +114,6 @@ inline size_t ws_round(size_t bytes) { return (bytes + 255) & ~size_t(255); }
 inline cudaStream_t as_cuda(ifci_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
 
 int device_sm_count(int device);
+int launch_exc_blocks(ifci_handle_t h, int nstr, int nexc, const int32_t *exc, uint8_t *blk, cudaStream_t s);
 
 }  // namespace ifci

@@ -5,6 +5,7 @@
 
 #include "dav_driver.cuh"
 #include "hamiltonian.cuh"
+#include "tc_gather.cuh"
 
 namespace ifci {
 
@@ -24,7 +25,8 @@ static void dav_layout(const std::vector<ProbSpec> &specs, const ifci_davidson_o
         int np = p.n * (p.n + 1) / 2;
         if (!cls.count({p.n, p.m})) {
             cls[{p.n, p.m}] = (int)cls.size();
-            z.bytes += ws_round((size_t)nstr * 8) + ws_round((size_t)nstr * nexc * 4);
+            z.bytes += ws_round((size_t)nstr * 8) + ws_round((size_t)nstr * nexc * 4) +
+                       ws_round((size_t)nstr * kBlk16Stride);
         }
         z.bytes += ws_round((size_t)np * np * 8);                       // W
         if (lo) z.bytes += ws_round((size_t)np * np * 4);               // Wf
@@ -37,7 +39,7 @@ static void dav_layout(const std::vector<ProbSpec> &specs, const ifci_davidson_o
         z.sum_pd += (long long)np * ndet;
         z.n_items_sigma += (ndet + kGatherChunk - 1) / kGatherChunk;
         z.n_tiles_sigma += ((np + kGemmTM - 1) / kGemmTM) * ((ndet + kGemmTN - 1) / kGemmTN) +
-                           ((ndet + 127) / 128) * ((np + oz_tile_n() - 1) / oz_tile_n());
+                           tcg::row_tile_count(nstr) * ((np + oz_tile_n() - 1) / oz_tile_n() + 1);
     }
     size_t n = specs.size();
     z.nclass = (int)cls.size();
@@ -100,6 +102,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
 
     // string tables per class
     std::map<std::pair<int, int>, std::pair<uint64_t *, int32_t *>> tables;
+    std::map<std::pair<int, int>, uint8_t *> blocks;
     for (const ProbSpec &p : specs) {
         auto key = std::make_pair(p.n, p.m);
         if (tables.count(key)) continue;
@@ -111,6 +114,10 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
         if (!st || !ex) return set_error(h, IFCI_ERR_OOM, "davidson: workspace (strings)");
         IFCI_TRY(ifci_build_strings(h, p.n, p.m, st, ex, (ifci_stream_t)s));
         tables[key] = {st, ex};
+        uint8_t *bl = ws_take<uint8_t>(h, (size_t)nstr * kBlk16Stride);
+        if (!bl) return set_error(h, IFCI_ERR_OOM, "davidson: workspace (block table)");
+        IFCI_TRY(launch_exc_blocks(h, nstr, nexc, ex, bl, s));
+        blocks[key] = bl;
     }
 
     DavBatch b;
@@ -162,6 +169,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
         SigmaProb sp{};
         sp.n = p.n; sp.nstr = nstr; sp.nexc = nexc; sp.np = np; sp.ld = np;
         sp.ndet = ndet; sp.stride = ndet; sp.exc = tb.second;
+        sp.blk = blocks[{p.n, p.m}];
         sp.W = W; sp.Wf = Wf; sp.Wtc = Wtc;
         sp.Woz = Woz;
         sp.Wexp = oz ? (double *)(Woz + (oz_operand_bytes(np) - np * 8 - 256)) : nullptr;

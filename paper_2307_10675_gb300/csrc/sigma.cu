@@ -11,6 +11,7 @@
 // D and G are pair-major planes [A][K] so that the alpha parts (whole rows
 // c[J_alpha][:]) are read and written with consecutive K across a warp.
 #include "sigma.cuh"
+#include "tc_gather.cuh"
 
 namespace ifci {
 
@@ -140,6 +141,61 @@ scatter_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__
     s[I] = v;
 }
 
+// Quantised copy of c for the tensor-core gathers, written into the D buffer
+// (which those paths do not need): FP32 for BF16, and for FP64E the fixed
+// point integer round(c * 2^38 / dscale), so that their gathers run in FP32 or
+// integer arithmetic (GB300 issues FP64 at a small fraction of FP32).
+template <int KIND>
+__global__ void __launch_bounds__(kGatherChunk)
+quantise_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__ items, char *__restrict__ qbuf) {
+    const WorkItem it = items[blockIdx.x];
+    const SigmaProb &p = probs[it.prob];
+    if (p.active && !*p.active) return;
+    const long long I = it.start + threadIdx.x;
+    if (I >= p.ndet) return;
+    const double *c = p.cbase + (p.cslot ? (long long)*p.cslot : 0ll) * p.stride;
+    const long long off = p.qoff;
+    if (KIND == 0) {
+        reinterpret_cast<float *>(qbuf)[off + I] = (float)c[I];
+    } else {
+        const double sc = 274877906944.0 / p.dscale;   // 2^38 / dscale
+        reinterpret_cast<long long *>(qbuf)[off + I] = __double2ll_rn(c[I] * sc);
+    }
+}
+
+// Scatter of the FP64-emulating path: G is int64 fixed point with one scale
+// per problem (2^-45 Wscale dscale), so sigma_I sums integers exactly and
+// converts once.
+__global__ void __launch_bounds__(kGatherChunk)
+scatter_fixed_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__ items,
+                     const long long *__restrict__ G) {
+    const WorkItem it = items[blockIdx.x];
+    const SigmaProb &p = probs[it.prob];
+    if (p.active && !*p.active) return;
+    const long long I = it.start + threadIdx.x;
+    if (I >= p.ndet) return;
+    const int nstr = p.nstr, nexc = p.nexc;
+    const long long ndet = p.ndet;
+    const int ia = (int)(I / nstr), ib = (int)(I % nstr);
+    const int32_t *__restrict__ ea = p.exc + (size_t)ia * nexc;
+    const int32_t *__restrict__ eb = p.exc + (size_t)ib * nexc;
+    const long long *__restrict__ Gp = G + p.doff;
+    long long acc = 0;
+    for (int e = 0; e < nexc; e++) {
+        const int32_t x = ea[e];
+        const long long gv = Gp[(long long)exc_pair(x) * ndet + (long long)exc_J(x) * nstr + ib];
+        acc += (x & 1) ? -gv : gv;
+    }
+    const long long rowb = (long long)ia * nstr;
+    for (int e = 0; e < nexc; e++) {
+        const int32_t x = eb[e];
+        const long long gv = Gp[(long long)exc_pair(x) * ndet + rowb + exc_J(x)];
+        acc += (x & 1) ? -gv : gv;
+    }
+    double *s = p.sbase + (p.sslot ? (long long)*p.sslot : 0ll) * p.stride;
+    s[I] = (double)acc * (p.Wexp[0] * p.dscale * 0x1p-45);
+}
+
 int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision) {
     plan.waves.clear();
     plan.items.clear();
@@ -147,7 +203,7 @@ int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision
     plan.tctiles.clear();
     plan.max_delems = 0;
     const bool tc = precision == IFCI_BF16 || precision == IFCI_TF32;
-    SigmaWave w{0, 0, 0, 0, 0, 0, 0};
+    SigmaWave w{0, 0, 0, 0, 0, 0, 0, 0};
     for (size_t i = 0; i < plan.probs.size(); i++) {
         SigmaProb &p = plan.probs[i];
         long long need = (long long)p.np * p.ndet;
@@ -157,27 +213,29 @@ int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision
         if (w.delems + need > budget) {
             plan.max_delems = std::max(plan.max_delems, w.delems);
             plan.waves.push_back(w);
-            w = SigmaWave{(int)plan.items.size(), 0, (int)plan.tiles.size(), 0, (int)plan.tctiles.size(), 0, 0};
+            w = SigmaWave{(int)plan.items.size(), 0, (int)plan.tiles.size(), 0, (int)plan.tctiles.size(), 0, 0, 0};
         }
         p.doff = w.delems;
         w.delems += need;
+        p.qoff = w.qelems;
+        w.qelems += p.ndet;
         for (long long s0 = 0; s0 < p.ndet; s0 += kGatherChunk) {
             plan.items.push_back(WorkItem{(int)i, 0, s0});
             w.nitem++;
         }
         if (tc) {
-            // one tile = 128 determinants x all pairs (see sigma_tc.cu)
-            for (long long s0 = 0; s0 < p.ndet; s0 += 128) {
-                plan.tctiles.push_back(WorkItem{(int)i, 0, s0});
-                w.ntc++;
-            }
+            // one tile = up to 128 determinants of whole alpha rows x all pairs (sigma_tc.cu)
+            size_t before = plan.tctiles.size();
+            tcg::append_row_tiles(plan.tctiles, (int)i, 0, p.nstr);
+            w.ntc += (int)(plan.tctiles.size() - before);
         } else if (precision == IFCI_FP64E) {
-            // one tile = 128 determinants x oz_tile_n() output pairs (see sigma_oz.cu)
-            for (long long s0 = 0; s0 < p.ndet; s0 += 128)
-                for (int n0 = 0; n0 < p.np; n0 += oz_tile_n()) {
-                    plan.tctiles.push_back(WorkItem{(int)i, n0, s0});
-                    w.ntc++;
-                }
+            // one tile = up to 128 determinants x oz_tile_n() output pairs (sigma_oz.cu);
+            // the output-pair tiles of a problem run back to back so W stays resident longer
+            for (int n0 = 0; n0 < p.np; n0 += oz_tile_n()) {
+                size_t before = plan.tctiles.size();
+                tcg::append_row_tiles(plan.tctiles, (int)i, n0, p.nstr);
+                w.ntc += (int)(plan.tctiles.size() - before);
+            }
         } else {
             for (int m0 = 0; m0 < p.np; m0 += kGemmTM)
                 for (long long s0 = 0; s0 < p.ndet; s0 += kGemmTN) {
@@ -257,12 +315,22 @@ int run_sigma(ifci_handle_t h, const SigmaPlan &plan, int precision, void *D, vo
                                                                    (const float *)G);
             IFCI_LAUNCH_CHECK(h);
         } else if (precision == IFCI_FP64E) {
-            IFCI_TRY(launch_oz_contract(h, plan, w, G, s));
+            {
+                ProfScope ps(h, s, PK_GATHER);
+                quantise_kernel<1><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0, (char *)D);
+                IFCI_LAUNCH_CHECK(h);
+            }
+            IFCI_TRY(launch_oz_contract(h, plan, w, D, G, s));
             ProfScope ps(h, s, PK_SCATTER);
-            scatter_kernel<double><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
-                                                                    (const double *)G);
+            scatter_fixed_kernel<<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
+                                                                  (const long long *)G);
             IFCI_LAUNCH_CHECK(h);
         } else {
+            {
+                ProfScope ps(h, s, PK_GATHER);
+                quantise_kernel<0><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0, (char *)D);
+                IFCI_LAUNCH_CHECK(h);
+            }
             IFCI_TRY(launch_tc_contract(h, plan, w, precision, D, G, s));
             ProfScope ps(h, s, PK_SCATTER);
             scatter_kernel<float><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,

@@ -14,12 +14,14 @@ struct SigmaProb {
     long long ndet;
     long long stride;
     const int32_t *exc;      // [nstr * nexc] excitation table of (n, nelec_spin)
+    const uint8_t *blk;      // [nstr * kBlk16Stride] entry offsets per 16-pair block (tensor-core paths)
     const double *W;         // [ld * ld] folded contraction matrix, FP64
     const float *Wf;         // [ld * ld] FP32 copy (FP32 path) or nullptr
     const void *Wtc;         // tensor-core operand image (BF16 path) or nullptr
     const void *Woz;         // sliced operand image of the FP64-emulating path or nullptr
     double *Wexp;            // [np] power-of-two row scales of Woz
     double dscale;           // power of two >= max |D| (FP64-emulating path)
+    long long qoff;          // element offset of the quantised copy of c in its wave buffer
     const double *cbase;
     double *sbase;
     const int *cslot;        // device slot index or nullptr (= 0)
@@ -42,6 +44,7 @@ struct SigmaWave {
     int tile0, ntile;        // contraction tiles
     int tc0, ntc;            // tensor-core tiles (BF16/TF32)
     long long delems;        // D (and G) elements of the wave
+    long long qelems;        // elements of the quantised copies of c (sum of ndet)
 };
 
 // Host-side plan over a fixed problem set; device arrays live in caller memory.
@@ -69,7 +72,8 @@ size_t sigma_elem_bytes(int precision);
 int oz_operand_bytes(int np);                  // bytes of one problem's sliced W image (+ row scales)
 int oz_tile_n();                               // output pairs per tile
 int launch_oz_pack_w(ifci_handle_t h, int nprob, const SigmaProb *d_probs, cudaStream_t s);
-int launch_oz_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &w, void *G, cudaStream_t s);
+int launch_oz_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &w, const void *Q, void *G,
+                       cudaStream_t s);
 int launch_oz_dscale(ifci_handle_t h, SigmaProb *d_prob, const double *c, long long n, cudaStream_t s);
 
 // tensor-core contraction (sigma_tc.cu)

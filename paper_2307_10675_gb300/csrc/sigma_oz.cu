@@ -4,23 +4,30 @@
 // that must be exact to FP64 level (Davidson restart vectors, final Rayleigh
 // quotients) are emulated with integer slices (an Ozaki-style splitting):
 //
-//   W[A][B] = 2^{e_A} 2^-7 (w1 + 2^-8 w2 + ... + 2^-32 w5)    per output row A
-//   D[B][K] = dscale  2^-7 (d1 + 2^-8 d2 + ... + 2^-32 d5)    dscale >= max|D|
+//   W[A][B] = Wscale 2^-7 (w1 + 2^-8 w2 + ... + 2^-32 w5)    Wscale >= max|W|
+//   D[B][K] = dscale  2^-6 (d1 + 2^-8 d2 + ... + 2^-32 d5)    dscale >= max|D|
 //
-// with every slice an integer in [-128, 128], exact in BF16.  The product of
-// two slices over K <= 204 terms stays below 2^24 even when the (up to five)
+// with every slice an integer in [-128, 128], exact in BF16.  D comes from the
+// fixed-point copy round(c 2^38 / dscale) of the input vector (quantise_kernel),
+// so the gather adds integers and the slices are the base-256 digits of
+// X + 128 (1 + 2^8 + ... + 2^32) minus 128: no FP64 arithmetic in this kernel.
+// The product of two slices over K <= 204 terms stays below 2^24 even when the (up to five)
 // slice pairs of one scale level L = i + j share an accumulator, so each level
 // is summed exactly by the tensor cores in FP32.  The 15 slice pairs with
-// i + j <= 4 (0-based) are kept; the epilogue combines the five levels in
-// FP64: G = 2^{e_A} dscale 2^-14 sum_L 2^{-8L} acc_L.  The dropped terms and
-// the slice truncation leave a relative error of order 2^-38 of max|W| max|D|.
+// i + j <= 4 (0-based) are kept; the epilogue combines the five levels exactly
+// in int64, G = 2^-45 Wscale dscale sum_L 2^{8 (4 - L)} acc_L, and stores the
+// integer; the scatter sums those integers and converts once per determinant
+// (no FP64 arithmetic in the hot loop).  The dropped terms and the slice
+// truncation leave a relative error of order 2^-38 of max|W| max|D|.
 //
 // Tile: 128 determinants (TMEM lanes) x 96 output pairs; five accumulators
 // of 96 FP32 columns (480 of the 512 TMEM columns).  K runs in 64-pair atoms:
-// for each atom the W slices (5 x 96 x 64 BF16, pre-swizzled image) arrive by
-// one bulk async copy while the 128 threads build the five D slices of their
-// determinants (fused gather), then one thread issues the 15 x 4 MMAs.
+// the W slices of the next atom (5 x 96 x 64 BF16, pre-swizzled image) arrive
+// by bulk async copy into the second stage buffer while 512 threads (four per
+// determinant) build the five D slices of the current atom, then one thread
+// issues the 15 x 4 MMAs.
 #include "sigma.cuh"
+#include "tc_gather.cuh"
 #include "tcgen05.cuh"
 
 namespace ifci {
@@ -31,10 +38,12 @@ using namespace tc;
 
 constexpr int kS = 5;                       // slices per operand
 constexpr int kNT = 96;                     // output pairs per tile
+constexpr int kThreads = 512;               // 4 threads per determinant row
 constexpr int kOzTmemCols = 512;
 constexpr int kMaxNpExact = 204;            // exact level sums need npair <= 204
 constexpr size_t kWStage = (size_t)kS * kNT * kAtomBytes;     // 61,440 B
 constexpr size_t kAStage = (size_t)kS * kTM * kAtomBytes;     // 81,920 B
+constexpr long long kDigitBias = 128ll * 0x0101010101ll;      // 128 in each of the five digits
 
 __host__ __device__ inline int n_tiles(int np) { return (np + kNT - 1) / kNT; }
 
@@ -54,17 +63,46 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-__global__ void __launch_bounds__(kTM, 1)
+// The CTA's sequence of W stages: (tile t, atom a) over its active tiles.
+struct StageCursor {
+    int t, a;
+};
+
+__device__ __forceinline__ bool tile_active(const SigmaProb *probs, const WorkItem *tiles, int t) {
+    const SigmaProb &p = probs[tiles[t].prob];
+    return !(p.active && !*p.active);
+}
+
+// next stage after (t, a) within [t, t1), skipping inactive tiles; t = t1 when none
+__device__ __forceinline__ StageCursor next_stage(const SigmaProb *probs, const WorkItem *tiles, StageCursor c,
+                                                  int t1) {
+    const int KA = k_atoms(probs[tiles[c.t].prob].np);
+    if (c.a + 1 < KA) return StageCursor{c.t, c.a + 1};
+    int t = c.t + 1;
+    while (t < t1 && !tile_active(probs, tiles, t)) t++;
+    return StageCursor{t, 0};
+}
+
+__device__ __forceinline__ const uint8_t *stage_src(const SigmaProb *probs, const WorkItem *tiles, StageCursor c) {
+    const WorkItem tile = tiles[c.t];
+    const SigmaProb &p = probs[tile.prob];
+    const int KA = k_atoms(p.np), nt = tile.sub / kNT;
+    return (const uint8_t *)p.Woz + ((size_t)nt * KA + c.a) * kWStage;
+}
+
+// G[A][K] (int64, fixed point 2^-45 Wscale dscale) for one tile of 128 determinants x 96 pairs.
+__global__ void __launch_bounds__(kThreads, 1)
 oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__ tiles, int ntile,
-                   double *__restrict__ G, int *__restrict__ err) {
+                   const long long *__restrict__ Q, long long *__restrict__ G, int *__restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bar_w, bar_mma;
+    __shared__ __align__(8) uint64_t bar_w[2], bar_mma;
     __shared__ uint32_t tmem_slot;
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *Wsm = base;                    // [slice i][kNT rows][128 B]
-    uint8_t *Asm = base + kWStage;          // [slice j][128 rows][128 B]
+    uint8_t *Wsm0 = base;                   // two W stages: [slice i][kNT rows][128 B]
+    uint8_t *Asm = base + 2 * kWStage;      // [slice j][128 rows][128 B]
     const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t bw = smem_u32(&bar_w), bm = smem_u32(&bar_mma);
+    const int row = tid & (kTM - 1), q = tid >> 7;   // determinant row of the tile, quarter
+    const uint32_t bw0 = smem_u32(&bar_w[0]), bw1 = smem_u32(&bar_w[1]), bm = smem_u32(&bar_mma);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -73,7 +111,8 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(bw, 1);
+        mbar_init(bw0, 1);
+        mbar_init(bw1, 1);
         mbar_init(bm, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -84,64 +123,76 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
 
     const int per = (ntile + gridDim.x - 1) / gridDim.x;
     const int t0 = blockIdx.x * per, t1 = min(ntile, t0 + per);
-    uint32_t ph_w = 0, ph_m = 0;
+    uint32_t ph_m = 0;
+    uint32_t g = 0;            // W stages consumed so far: buffer g & 1, phase (g >> 1) & 1
     bool ok = true;
-    for (int t = t0; t < t1 && ok; t++) {
+    int tfirst = t0;
+    while (tfirst < t1 && !tile_active(probs, tiles, tfirst)) tfirst++;
+    if (tid == 0 && tfirst < t1) bulk_load(smem_u32(Wsm0), stage_src(probs, tiles, StageCursor{tfirst, 0}),
+                                           (uint32_t)kWStage, bw0);
+    for (int t = tfirst; t < t1 && ok;) {
         const WorkItem tile = tiles[t];
         const SigmaProb &p = probs[tile.prob];
-        if (p.active && !*p.active) continue;
-        const int np = p.np, KA = k_atoms(np), n0 = tile.sub, nt = n0 / kNT;
+        const int np = p.np, KA = k_atoms(np), n0 = tile.sub;
         const int Nt = round_up(min(kNT, np - n0), 16);
         const long long ndet = p.ndet;
-        const long long K = tile.start + tid;
-        const bool live = K < ndet;
         const int nstr = p.nstr, nexc = p.nexc;
-        const int ka = live ? (int)(K / nstr) : 0, kb = live ? (int)(K % nstr) : 0;
-        const double *c = p.cbase + (p.cslot ? (long long)*p.cslot : 0ll) * p.stride;
-        const int32_t *ea = p.exc + (size_t)ka * nexc;
-        const int32_t *eb = p.exc + (size_t)kb * nexc;
-        const double *crow = c + (long long)ka * nstr;
-        const double inv_ds = 1.0 / p.dscale;
-        int ia = 0, ib = 0;
-        int32_t xa = live ? ea[0] : 0, xb = live ? eb[0] : 0;
-        int pa = live ? exc_pair(xa) : -1, pb = live ? exc_pair(xb) : -1;
-        uint32_t started = 0;   // accumulator levels already written in this tile
-        const uint8_t *wimg = (const uint8_t *)p.Woz + (size_t)nt * KA * kWStage;
-        for (int a = 0; a < KA && ok; a++) {
-            if (tid == 0) bulk_load(smem_u32(Wsm), wimg + (size_t)a * kWStage, (uint32_t)kWStage, bw);
-            // ---- fused gather of pairs [64a, 64a + 64) and slicing into kS BF16 atoms
-            uint8_t *row = Asm + tid * kAtomBytes;
-            for (int ch = 0; ch < 8; ch++) {
-                float sl[8][kS];
+        const tcg::TileGeom geo = tcg::tile_geom(tile.start, nstr);
+        const bool live = row < geo.R * geo.Cw;
+        const int r = live ? row / geo.Cw : 0;
+        const int ka = geo.ka0 + r, kb = geo.kb0 + (live ? row % geo.Cw : 0);
+        const long long K = (long long)ka * nstr + kb;
+        const long long *C = Q + p.qoff;   // round(c 2^38 / dscale)
+        uint32_t started = 0;      // accumulator levels already written in this tile
+        for (int a = 0; a < KA; a++, g++) {
+            // ---- loads of this atom's block (pairs 64a + 16q .. + 16): they overlap
+            // the MMAs of the previous atom, which are still running
+            const int b = 4 * a + q;
+            long long x[16];
+#pragma unroll
+            for (int k = 0; k < 16; k++) x[k] = 0;
+            if (live) tcg::gather_block16<long long>(p, C, ka, kb, b, x);
+            if (a > 0) {
+                if (!__syncthreads_and(mbar_wait(bm, ph_m))) { ok = false; break; }
+                ph_m ^= 1;
+            }
+            // the A buffer and W buffer (g + 1) & 1 are free now: prefetch the next stage
+            const StageCursor nx = next_stage(probs, tiles, StageCursor{t, a}, t1);
+            if (tid == 0 && nx.t < t1)
+                bulk_load(smem_u32(Wsm0 + ((g + 1) & 1) * kWStage), stage_src(probs, tiles, nx), (uint32_t)kWStage,
+                          ((g + 1) & 1) ? bw1 : bw0);
+            // ---- five digit slices of the block, two 16-byte chunks per slice
+#pragma unroll
+            for (int half = 0; half < 2; half++) {
+                uint32_t lo[8], hi[8];
 #pragma unroll
                 for (int e = 0; e < 8; e++) {
-                    const int A = a * 64 + ch * 8 + e;
-                    double v = 0.0;
-                    if (pa == A) {
-                        v += exc_sign(xa) * c[(long long)exc_J(xa) * nstr + kb];
-                        if (++ia < nexc) { xa = ea[ia]; pa = exc_pair(xa); } else pa = -1;
-                    }
-                    if (pb == A) {
-                        v += exc_sign(xb) * crow[exc_J(xb)];
-                        if (++ib < nexc) { xb = eb[ib]; pb = exc_pair(xb); } else pb = -1;
-                    }
-                    slice5(v * inv_ds, sl[e]);
+                    const unsigned long long Xb = (unsigned long long)(x[8 * half + e] + kDigitBias);
+                    lo[e] = (uint32_t)Xb;
+                    hi[e] = (uint32_t)(Xb >> 32);
                 }
-                const int sw = (ch ^ (tid & 7)) << 4;
+                const int ch = 2 * q + half;
+                uint8_t *dst = Asm + row * kAtomBytes + ((ch ^ (row & 7)) << 4);
 #pragma unroll
                 for (int j = 0; j < kS; j++) {
-                    uint4 q = make_uint4(pack2(sl[0][j], sl[1][j]), pack2(sl[2][j], sl[3][j]),
-                                         pack2(sl[4][j], sl[5][j]), pack2(sl[6][j], sl[7][j]));
-                    *(uint4 *)(row + (size_t)j * kTM * kAtomBytes + sw) = q;
+                    const int d = kS - 1 - j;          // slice j = digit d (j = 0 most significant)
+                    uint32_t w4[4];
+#pragma unroll
+                    for (int e = 0; e < 8; e += 2) {
+                        const uint32_t u0 = d == 4 ? (hi[e] & 255u) : ((lo[e] >> (8 * d)) & 255u);
+                        const uint32_t u1 = d == 4 ? (hi[e + 1] & 255u) : ((lo[e + 1] >> (8 * d)) & 255u);
+                        w4[e / 2] = pack_bf16x2f((float)((int)u0 - 128), (float)((int)u1 - 128));
+                    }
+                    *(uint4 *)(dst + (size_t)j * kTM * kAtomBytes) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            if (!__syncthreads_and(mbar_wait(bw, ph_w))) { ok = false; break; }
-            ph_w ^= 1;
+            const uint32_t bwg = (g & 1) ? bw1 : bw0;
+            if (!__syncthreads_and(mbar_wait(bwg, (g >> 1) & 1))) { ok = false; break; }
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t idesc = idesc_bf16(kTM, Nt);
-                const uint32_t a0 = smem_u32(Asm), w0 = smem_u32(Wsm);
+                const uint32_t a0 = smem_u32(Asm), w0 = smem_u32(Wsm0 + (g & 1) * kWStage);
                 const int kst = min(4, (round_up(np, 16) - a * 64) / 16);
                 for (int j = 0; j < kS; j++) {
                     for (int i = 0; i + j < kS; i++) {
@@ -158,40 +209,45 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
                 mma_commit(bm);
             }
             __syncwarp();
-            if (!__syncthreads_and(mbar_wait(bm, ph_m))) { ok = false; break; }
+        }
+        // the MMAs of the tile's last atom
+        if (ok) {
+            if (!__syncthreads_and(mbar_wait(bm, ph_m))) ok = false;
             ph_m ^= 1;
         }
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // ---- epilogue: combine the levels in FP64, scale, store G[A][K]
-        double *Gp = G + p.doff;
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        const double ds = p.dscale * (1.0 / 16384.0);
-        for (int c0 = 0; c0 < Nt; c0 += 16) {
-            double g[16];
+        // ---- epilogue: the levels are exact integers below 2^24; combine them
+        // in int64, G = sum_L acc_L 2^{8 (4 - L)}  (no FP64 arithmetic)
+        long long *Gp = G + p.doff;
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        for (int c0 = 16 * (warp >> 2); c0 < Nt; c0 += 64) {
+            long long gi[16];
 #pragma unroll
-            for (int j = 0; j < 16; j++) g[j] = 0.0;
-            double wL = 1.0;
+            for (int j = 0; j < 16; j++) gi[j] = 0;
 #pragma unroll
             for (int L = 0; L < kS; L++) {
                 float v[16];
                 tmem_ld16(tmem + lane_base + (uint32_t)(L * kNT + c0), v);
 #pragma unroll
-                for (int j = 0; j < 16; j++) g[j] += wL * (double)v[j];
-                wL *= 1.0 / 256.0;
+                for (int j = 0; j < 16; j++) gi[j] += (long long)__float2int_rn(v[j]) << (8 * (kS - 1 - L));
             }
             if (live) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
                     const int A = n0 + c0 + j;
-                    if (c0 + j < Nt && A < np && A < n0 + kNT) Gp[(long long)A * ndet + K] = g[j] * ds * p.Wexp[A];
+                    if (c0 + j < Nt && A < np) Gp[(long long)A * ndet + K] = gi[j];
                 }
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
+        t++;
+        while (t < t1 && !tile_active(probs, tiles, t)) t++;
     }
     if (!ok && tid == 0) atomicExch(err, 1);
+    // a prefetch may still be in flight after a timeout: wait for it (bounded)
+    if (!ok) __syncthreads_and(mbar_wait((g & 1) ? bw1 : bw0, (g >> 1) & 1));
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
@@ -199,37 +255,43 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
                      : "memory");
 }
 
-// Sliced image of W: [tile nt][atom a][slice i][kNT rows][128 B], rows n0 + r
-// of W scaled by 2^-e (e: smallest power with max_k |W[n][k]| <= 2^e), the
+// Sliced image of W: [tile nt][atom a][slice i][kNT rows][128 B], W scaled by
+// 2^-e with one exponent per problem (max |W| <= 2^e, stored in Wexp[0]), the
 // 16-byte chunk c of a row at c ^ (row % 8), zeros beyond npair.
 __global__ void oz_pack_w_kernel(const SigmaProb *__restrict__ probs) {
     const SigmaProb &p = probs[blockIdx.x];
     const int np = p.np, KA = k_atoms(np), NTl = n_tiles(np);
     uint8_t *img = (uint8_t *)const_cast<void *>(p.Woz);
-    for (int n = threadIdx.x; n < np; n += blockDim.x) {
-        double mx = 0.0;
-        for (int k = 0; k < np; k++) mx = fmax(mx, fabs(p.W[(long long)n * p.ld + k]));
-        int e = 0;
-        if (mx > 0.0) frexp(mx, &e);          // mx = f 2^e, f in [0.5, 1)
-        p.Wexp[n] = ldexp(1.0, e);
-    }
+    __shared__ double red[256];
+    double mx = 0.0;
+    for (long long i = threadIdx.x; i < (long long)np * np; i += blockDim.x)
+        mx = fmax(mx, fabs(p.W[(i / np) * p.ld + i % np]));
+    red[threadIdx.x] = mx;
     __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    int e = 0;
+    if (red[0] > 0.0) frexp(red[0], &e);          // max = f 2^e, f in [0.5, 1)
+    const double scale = ldexp(1.0, e);
+    if (threadIdx.x == 0) p.Wexp[0] = scale;
     const int rows = NTl * kNT;
     for (int t = threadIdx.x; t < rows * KA * 8; t += blockDim.x) {
         const int n = t / (KA * 8), rest = t % (KA * 8), a = rest / 8, ch = rest % 8;
         const int nt = n / kNT, r = n % kNT;
         float sl[8][kS];
-        for (int e = 0; e < 8; e++) {
-            const int k = a * 64 + ch * 8 + e;
-            double x = (n < np && k < np) ? p.W[(long long)n * p.ld + k] / p.Wexp[n] : 0.0;
-            slice5(x, sl[e]);
+        for (int e2 = 0; e2 < 8; e2++) {
+            const int k = a * 64 + ch * 8 + e2;
+            double x = (n < np && k < np) ? p.W[(long long)n * p.ld + k] / scale : 0.0;
+            slice5(x, sl[e2]);
         }
         for (int i = 0; i < kS; i++) {
-            uint4 q = make_uint4(pack2(sl[0][i], sl[1][i]), pack2(sl[2][i], sl[3][i]), pack2(sl[4][i], sl[5][i]),
-                                 pack2(sl[6][i], sl[7][i]));
+            uint4 qv = make_uint4(pack2(sl[0][i], sl[1][i]), pack2(sl[2][i], sl[3][i]), pack2(sl[4][i], sl[5][i]),
+                                  pack2(sl[6][i], sl[7][i]));
             size_t off = (((size_t)nt * KA + a) * kS + i) * (kNT * kAtomBytes) + (size_t)r * kAtomBytes +
                          ((ch ^ (r & 7)) << 4);
-            *(uint4 *)(img + off) = q;
+            *(uint4 *)(img + off) = qv;
         }
     }
 }
@@ -277,13 +339,14 @@ int launch_oz_dscale(ifci_handle_t h, SigmaProb *d_prob, const double *c, long l
     return IFCI_OK;
 }
 
-int launch_oz_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &w, void *G, cudaStream_t s) {
+int launch_oz_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &w, const void *Q, void *G,
+                       cudaStream_t s) {
     if (w.ntc == 0) return IFCI_OK;
     for (const SigmaProb &p : plan.probs)
         if (p.np > kMaxNpExact)
             return set_error(h, IFCI_ERR_UNSUPPORTED, "FP64E: npair %d > %d (exact level sums)", p.np, kMaxNpExact);
     if (!h->d_err) return set_error(h, IFCI_ERR_INVALID_ARG, "FP64E: no error flag");
-    const size_t smem = 1024 + kWStage + kAStage;
+    const size_t smem = 1024 + 2 * kWStage + kAStage;   // 205,824 B
     static bool configured = false;
     if (!configured) {
         IFCI_CUDA_TRY(h, cudaFuncSetAttribute(oz_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -291,8 +354,9 @@ int launch_oz_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &
         configured = true;
     }
     const int grid = std::min(w.ntc, device_sm_count(h->device));
-    ProfScope ps(h, s, PK_CONTRACT);
-    oz_contract_kernel<<<grid, kTM, smem, s>>>(plan.d_probs, plan.d_tctiles + w.tc0, w.ntc, (double *)G, h->d_err);
+    ProfScope ps(h, s, PK_CONTRACT_HI);
+    oz_contract_kernel<<<grid, kThreads, smem, s>>>(plan.d_probs, plan.d_tctiles + w.tc0, w.ntc,
+                                                    (const long long *)Q, (long long *)G, h->d_err);
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;
 }

@@ -16,6 +16,7 @@
 // at problem boundaries.  Every mbarrier wait is bounded; on a timeout the
 // kernel records an error flag, frees its TMEM and returns.
 #include "sigma.cuh"
+#include "tc_gather.cuh"
 #include "tcgen05.cuh"
 
 namespace ifci {
@@ -24,9 +25,18 @@ namespace {
 
 using namespace tc;
 
-__global__ void __launch_bounds__(kTM, 1)
+constexpr int kBfThreads = 512;   // four threads per determinant row
+
+__device__ __forceinline__ void store_bf16(uint8_t *Asm, int row, int A, float v) {
+    const int off = (A >> 6) * (kTM * kAtomBytes) + row * kAtomBytes + ((((A >> 3) & 7) ^ (row & 7)) << 4) +
+                    (A & 7) * 2;
+    *(__nv_bfloat16 *)(Asm + off) = __float2bfloat16_rn(v);
+}
+
+__global__ void __launch_bounds__(kBfThreads, 1)
 tc_contract_bf16_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__ tiles, int ntile,
-                        size_t w_bytes_max, float *__restrict__ G, int *__restrict__ err) {
+                        size_t w_bytes_max, size_t a_bytes_max, const float *__restrict__ Q,
+                        float *__restrict__ G, int *__restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_w, bar_mma;
     __shared__ uint32_t tmem_slot;
@@ -34,6 +44,7 @@ tc_contract_bf16_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__r
     uint8_t *Wsm = base;
     uint8_t *Asm = base + ((w_bytes_max + 1023) & ~(size_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & (kTM - 1), q = tid >> 7;            // determinant row, quarter
     const uint32_t bw = smem_u32(&bar_w), bm = smem_u32(&bar_mma);
 
     if (warp == 0) {
@@ -63,7 +74,8 @@ tc_contract_bf16_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__r
         const SigmaProb &p = probs[tile.prob];
         if (p.active && !*p.active) continue;
         const int np = p.np, N = n_pad(np), KA = k_atoms(np), KS = round_up(np, 16) / 16;
-        const long long ndet = p.ndet;
+        const int nstr = p.nstr, nexc = p.nexc;
+        const tcg::TileGeom geo = tcg::tile_geom(tile.start, nstr);
         if (tile.prob != cur) {
             if (tid == 0) bulk_load(smem_u32(Wsm), p.Wtc, (uint32_t)(KA * N * kAtomBytes), bw);
             // block-wide vote so that every thread leaves the loop together
@@ -71,48 +83,26 @@ tc_contract_bf16_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__r
             ph_w ^= 1;
             cur = tile.prob;
         }
-        // ---- fused gather: row tid of A = D^T of determinant K
-        const long long K = tile.start + tid;
-        {
-            const int nstr = p.nstr, nexc = p.nexc;
-            int ka = 0, kb = 0;
-            bool live = K < ndet;
-            if (live) {
-                ka = (int)(K / nstr);
-                kb = (int)(K % nstr);
-            }
-            const double *c = p.cbase + (p.cslot ? (long long)*p.cslot : 0ll) * p.stride;
-            const int32_t *ea = p.exc + (size_t)ka * nexc;
-            const int32_t *eb = p.exc + (size_t)kb * nexc;
-            int ia = 0, ib = 0;
-            int32_t xa = live ? ea[0] : 0, xb = live ? eb[0] : 0;
-            int pa = live ? exc_pair(xa) : -1, pb = live ? exc_pair(xb) : -1;
-            const double *crow = c + (long long)ka * nstr;
-            uint8_t *row = Asm + tid * kAtomBytes;
-            for (int ch = 0; ch < KA * 8; ch++) {
-                uint32_t pk[4];
+        // ---- fused gather: row `row` of A = D^T of determinant K; thread q owns the
+        // 16-pair blocks q, q + 4, ... and writes them as whole 16-byte chunks
+        const bool live = row < geo.R * geo.Cw;
+        const int r = live ? row / geo.Cw : 0;
+        const int ka = geo.ka0 + r, kb = geo.kb0 + (live ? row % geo.Cw : 0);
+        const long long K = (long long)ka * nstr + kb;
+        const float *c = Q + p.qoff;   // FP32 copy of the input vector
+        for (int b = q; b < KA * 4; b += 4) {
+            float x[16];
 #pragma unroll
-                for (int e = 0; e < 8; e += 2) {
-                    double v2[2];
+            for (int k = 0; k < 16; k++) x[k] = 0.0f;
+            if (live) tcg::gather_block16<float>(p, c, ka, kb, b, x);
 #pragma unroll
-                    for (int u = 0; u < 2; u++) {
-                        const int A = ch * 8 + e + u;
-                        double v = 0.0;
-                        if (pa == A) {
-                            v += exc_sign(xa) * c[(long long)exc_J(xa) * nstr + kb];
-                            if (++ia < nexc) { xa = ea[ia]; pa = exc_pair(xa); } else pa = -1;
-                        }
-                        if (pb == A) {
-                            v += exc_sign(xb) * crow[exc_J(xb)];
-                            if (++ib < nexc) { xb = eb[ib]; pb = exc_pair(xb); } else pb = -1;
-                        }
-                        v2[u] = v;
-                    }
-                    pk[e / 2] = pack_bf16x2(v2[0], v2[1]);
-                }
-                const int a = ch >> 3, cc = ch & 7;
-                uint4 *dst = (uint4 *)(row + a * (kTM * kAtomBytes) + ((cc ^ (tid & 7)) << 4));
-                *dst = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            for (int half = 0; half < 2; half++) {
+                const int ch = 2 * (b & 3) + half;   // chunk within the atom
+                uint4 w = make_uint4(pack_bf16x2f(x[8 * half + 0], x[8 * half + 1]),
+                                     pack_bf16x2f(x[8 * half + 2], x[8 * half + 3]),
+                                     pack_bf16x2f(x[8 * half + 4], x[8 * half + 5]),
+                                     pack_bf16x2f(x[8 * half + 6], x[8 * half + 7]));
+                *(uint4 *)(Asm + (b >> 2) * (kTM * kAtomBytes) + row * kAtomBytes + ((ch ^ (row & 7)) << 4)) = w;
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -134,13 +124,14 @@ tc_contract_bf16_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__r
         if (!__syncthreads_and(mbar_wait(bm, ph_m))) { ok = false; break; }
         ph_m ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // ---- epilogue: TMEM -> G[A][K]
+        // ---- epilogue: TMEM -> G[A][K]; warps sharing a TMEM lane quarter split the columns
         float *Gp = G + p.doff;
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        for (int c0 = 0; c0 < N; c0 += 16) {
+        const long long ndet = p.ndet;
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        for (int c0 = 16 * (warp >> 2); c0 < N; c0 += 64) {
             float v[16];
             tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
-            if (K < ndet) {
+            if (live) {
 #pragma unroll
                 for (int j = 0; j < 16; j++)
                     if (c0 + j < np) Gp[(long long)(c0 + j) * ndet + K] = v[j];
@@ -199,7 +190,7 @@ int launch_tc_pack_w(ifci_handle_t h, int nprob, const SigmaProb *d_probs, int p
 
 int launch_tc_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &w, int precision, const void *D,
                        void *G, cudaStream_t s) {
-    (void)D;
+    // D holds the FP32 copies of the input vectors (quantise_kernel)
     if (precision != IFCI_BF16) return set_error(h, IFCI_ERR_UNSUPPORTED, "tensor-core precision %d", precision);
     if (w.ntc == 0) return IFCI_OK;
     int max_np = 0;
@@ -209,6 +200,7 @@ int launch_tc_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &
     // at least 116 KB of shared memory: one CTA per SM, so TMEM allocation never waits
     const size_t smem = std::max(tc_smem_bytes(max_np), (size_t)116 * 1024);
     const size_t wmax = (size_t)k_atoms(max_np) * n_pad(max_np) * kAtomBytes;
+    const size_t amax = (size_t)k_atoms(max_np) * kTM * kAtomBytes;
     static int configured_smem = 0;
     if ((int)smem > configured_smem) {
         IFCI_CUDA_TRY(h, cudaFuncSetAttribute(tc_contract_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -217,8 +209,8 @@ int launch_tc_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &
     }
     const int grid = std::min(w.ntc, device_sm_count(h->device));
     ProfScope ps(h, s, PK_CONTRACT);
-    tc_contract_bf16_kernel<<<grid, kTM, smem, s>>>(plan.d_probs, plan.d_tctiles + w.tc0, w.ntc, wmax, (float *)G,
-                                                    h->d_err);
+    tc_contract_bf16_kernel<<<grid, kBfThreads, smem, s>>>(plan.d_probs, plan.d_tctiles + w.tc0, w.ntc, wmax, amax,
+                                                    (const float *)D, (float *)G, h->d_err);
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;
 }

@@ -1,0 +1,127 @@
+// Fused gather D^T = (E+ c)^T for the tensor-core contractions: tile geometry
+// and the two independent passes that fill the A operand in shared memory.
+//
+// A tile holds whole alpha-string rows of the CI vector: R rows x Cw columns
+// (R = 1 and Cw <= 128 when nstr >= 128; else R = min(16, 128 / nstr) rows of
+// all nstr columns).  Thread t owns determinant (ka0 + t / Cw, kb0 + t % Cw).
+// Four threads share a determinant row; each owns 16-pair blocks of it and
+// finds the alpha and beta excitations that land in its block through the
+// per-string table of list offsets per 16-pair block (lists are sorted by
+// pair).  The alpha part reads c[J_alpha][kb] with consecutive kb across a
+// warp (coalesced), the beta part c[ka][J_beta] from one row; both parts of
+// an element are summed in registers before its single conversion, and the
+// block is written to shared memory as whole 16-byte chunks.
+#pragma once
+#include "sigma.cuh"
+
+namespace ifci {
+namespace tcg {
+
+constexpr int kRows = 16;       // at most this many alpha rows per tile
+constexpr int kTileDets = 128;
+
+struct TileGeom {
+    int ka0, kb0, R, Cw;
+};
+
+__host__ __device__ inline TileGeom tile_geom(long long start, int nstr) {
+    TileGeom g;
+    g.ka0 = (int)(start / nstr);
+    g.kb0 = (int)(start % nstr);
+    if (nstr >= kTileDets) {
+        g.R = 1;
+        g.Cw = nstr - g.kb0 < kTileDets ? nstr - g.kb0 : kTileDets;
+    } else {
+        int rmax = kTileDets / nstr;
+        if (rmax > kRows) rmax = kRows;
+        g.R = nstr - g.ka0 < rmax ? nstr - g.ka0 : rmax;
+        g.Cw = nstr;
+    }
+    return g;
+}
+
+// Host: the row-aligned tiles of one problem, in order.
+inline void append_row_tiles(std::vector<WorkItem> &out, int prob, int sub, int nstr) {
+    if (nstr >= kTileDets) {
+        for (int ka = 0; ka < nstr; ka++)
+            for (int kb0 = 0; kb0 < nstr; kb0 += kTileDets)
+                out.push_back(WorkItem{prob, sub, (long long)ka * nstr + kb0});
+    } else {
+        int rmax = kTileDets / nstr;
+        if (rmax > kRows) rmax = kRows;
+        for (int ka0 = 0; ka0 < nstr; ka0 += rmax) out.push_back(WorkItem{prob, sub, (long long)ka0 * nstr});
+    }
+}
+
+inline long long row_tile_count(int nstr) {
+    if (nstr >= kTileDets) return (long long)nstr * ((nstr + kTileDets - 1) / kTileDets);
+    int rmax = kTileDets / nstr;
+    if (rmax > kRows) rmax = kRows;
+    return (nstr + rmax - 1) / rmax;
+}
+
+// amap[r][A] = index of pair A in the alpha list of row ka0 + r, or -1.
+// Called by all threads of the CTA; ends with __syncthreads().
+__device__ __forceinline__ void build_alpha_map(int16_t *amap, int np_pad, const SigmaProb &p, const TileGeom &g) {
+    const int nexc = p.nexc;
+    for (int i = threadIdx.x; i < g.R * np_pad; i += blockDim.x) amap[i] = -1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.R * nexc; i += blockDim.x) {
+        const int r = i / nexc, e = i % nexc;
+        const int32_t x = p.exc[(size_t)(g.ka0 + r) * nexc + e];
+        amap[r * np_pad + exc_pair(x)] = (int16_t)e;
+    }
+    __syncthreads();
+}
+
+}  // namespace tcg
+}  // namespace ifci
+
+namespace ifci {
+namespace tcg {
+
+// Sum of the alpha and beta contributions of determinant (ka, kb) to the 16
+// pairs [16 b, 16 b + 16): x[i] += sign * c.  T = float or long long.
+template <typename T>
+__device__ __forceinline__ void gather_block16(const SigmaProb &p, const T *__restrict__ c, int ka, int kb, int b,
+                                               T (&x)[16]) {
+    const int nstr = p.nstr, nexc = p.nexc;
+    const uint8_t *ba = p.blk + (size_t)ka * kBlk16Stride, *bb = p.blk + (size_t)kb * kBlk16Stride;
+    const int a0 = ba[b], a1 = ba[b + 1], b0 = bb[b], b1 = bb[b + 1];
+    const int32_t *ea = p.exc + (size_t)ka * nexc, *eb = p.exc + (size_t)kb * nexc;
+    const T *crow = c + (long long)ka * nstr;
+    const int base = 16 * b;
+    for (int e0 = a0; e0 < a1; e0 += 4) {
+        int32_t xe[4];
+        T v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) xe[u] = e0 + u < a1 ? ea[e0 + u] : 0;
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = e0 + u < a1 ? c[(long long)exc_J(xe[u]) * nstr + kb] : T(0);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int i = exc_pair(xe[u]) - base;
+            const T sv = (xe[u] & 1) ? -v[u] : v[u];
+#pragma unroll
+            for (int k = 0; k < 16; k++) x[k] += (e0 + u < a1 && i == k) ? sv : T(0);
+        }
+    }
+    for (int e0 = b0; e0 < b1; e0 += 4) {
+        int32_t ye[4];
+        T v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) ye[u] = e0 + u < b1 ? eb[e0 + u] : 0;
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = e0 + u < b1 ? crow[exc_J(ye[u])] : T(0);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int i = exc_pair(ye[u]) - base;
+            const T sv = (ye[u] & 1) ? -v[u] : v[u];
+#pragma unroll
+            for (int k = 0; k < 16; k++) x[k] += (e0 + u < b1 && i == k) ? sv : T(0);
+        }
+    }
+}
+
+}  // namespace tcg
+}  // namespace ifci

@@ -96,6 +96,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
 }
 
+__device__ __forceinline__ uint32_t pack_bf16x2f(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x = lo (low half), .y = hi
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(double lo, double hi) {
     __nv_bfloat16 a = __double2bfloat16(lo), b = __double2bfloat16(hi);
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);

@@ -104,10 +104,11 @@ def test_fp64e_sigma_exact_on_dyadic_inputs(handle, n, m):
 
 @pytest.mark.parametrize("X", [(0,), (0, 1), (5, 7), (8, 11, 12), (2, 9, 16), "six"])
 def test_fp64e_sigma_matches_fp64(handle, X):
-    """Slice truncation: five 8-bit slices leave 2^-40 of each operand's scale and
-    the dropped slice products are of the same order, so one element of G is off
-    by at most about npair * 2^-39 max|W| max|D| (3e-10 relative at npair = 171).
-    The test asks for 1e-10 relative in norm and 1e-9 of max|sigma| per element."""
+    """D is fixed point at 2^-38 dscale and W is sliced to 2^-40 of one scale
+    per problem (max|W|), so one element of G is off by at most about
+    npair (2^-38 + 2^-39) max|W| dscale, ~1e-9 of max|W| dscale at npair = 171,
+    and by ~sqrt(npair) less in norm.  The test asks for 5e-10 relative in norm
+    and 5e-9 of max|sigma| per element."""
     chain = chain_24_uneven()
     if X == "six":
         X = tuple(b for b, s in enumerate(chain.body_sizes) if s == 6)[:3]
@@ -120,8 +121,8 @@ def test_fp64e_sigma_matches_fp64(handle, X):
     s64e = ifci.ifci_sigma(handle, t, h1, eri, c, precision=ifci.IFCI_FP64E)
     torch.cuda.synchronize()
     a, b = s64e.cpu().numpy().reshape(-1), s64.cpu().numpy().reshape(-1)
-    assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)
-    assert np.max(np.abs(a - b)) <= 1e-9 * np.max(np.abs(b))
+    assert np.linalg.norm(a - b) <= 5e-10 * np.linalg.norm(b)
+    assert np.max(np.abs(a - b)) <= 5e-9 * np.max(np.abs(b))
 
 
 @pytest.mark.parametrize("prec,hi", [("fp64e", "fp64e"), ("bf16", "fp64e"), ("bf16", "fp64")])
