@@ -299,3 +299,34 @@ def ifci_rdm_backward(handle: Handle, system: SystemArrays, max_order: int, grad
     handle.check(_lib().ifci_rdm_backward(handle.ptr, system.as_c(), max_order, ctypes.byref(o), float(grad_out),
                                           _ptr(dh), _ptr(deri), 1 if recompute_vectors else 0, _stream(stream)))
     return dh, deri
+
+
+# ---------------------------------------------------------------- autograd
+
+class IfciEnergy(torch.autograd.Function):
+    """E_iFCI(h, V) with its gradient from ifci_rdm_backward.
+
+    forward(h (norb, norb) CUDA float64, V (npair, npair) CUDA float64, body_offset,
+    max_order, handle, opts) -> 0-d float64 tensor on h's device.  The
+    backward reuses the CI vectors the forward call kept in the handle; the
+    gradient with respect to the symmetric parameter V[A][B] = V[B][A] is the
+    sum of the two returned entries (see ifci_rdm_backward).
+    """
+
+    @staticmethod
+    def forward(ctx, h, V, body_offset, max_order, handle, opts=None):
+        sysd = SystemArrays(body_offset, h.detach(), V.detach())
+        out = ifci_increments(handle, sysd, max_order, opts)
+        ctx.state = (sysd, max_order, handle, opts)
+        return torch.tensor(out["e_total"], dtype=torch.float64, device=h.device)
+
+    @staticmethod
+    def backward(ctx, grad):
+        sysd, max_order, handle, opts = ctx.state
+        dh, dV = ifci_rdm_backward(handle, sysd, max_order, float(grad), opts, recompute_vectors=False)
+        return dh, dV, None, None, None, None
+
+
+def ifci_energy(h, V, body_offset, max_order, handle, opts=None):
+    """Differentiable E_iFCI (see IfciEnergy)."""
+    return IfciEnergy.apply(h, V, body_offset, max_order, handle, opts)

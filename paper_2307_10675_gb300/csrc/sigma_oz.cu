@@ -136,7 +136,7 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
         const int np = p.np, KA = k_atoms(np), n0 = tile.sub;
         const int Nt = round_up(min(kNT, np - n0), 16);
         const long long ndet = p.ndet;
-        const int nstr = p.nstr, nexc = p.nexc;
+        const int nstr = p.nstr;
         const tcg::TileGeom geo = tcg::tile_geom(tile.start, nstr);
         const bool live = row < geo.R * geo.Cw;
         const int r = live ? row / geo.Cw : 0;

@@ -27,12 +27,6 @@ using namespace tc;
 
 constexpr int kBfThreads = 512;   // four threads per determinant row
 
-__device__ __forceinline__ void store_bf16(uint8_t *Asm, int row, int A, float v) {
-    const int off = (A >> 6) * (kTM * kAtomBytes) + row * kAtomBytes + ((((A >> 3) & 7) ^ (row & 7)) << 4) +
-                    (A & 7) * 2;
-    *(__nv_bfloat16 *)(Asm + off) = __float2bfloat16_rn(v);
-}
-
 __global__ void __launch_bounds__(kBfThreads, 1)
 tc_contract_bf16_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__ tiles, int ntile,
                         size_t w_bytes_max, size_t a_bytes_max, const float *__restrict__ Q,
@@ -74,7 +68,7 @@ tc_contract_bf16_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__r
         const SigmaProb &p = probs[tile.prob];
         if (p.active && !*p.active) continue;
         const int np = p.np, N = n_pad(np), KA = k_atoms(np), KS = round_up(np, 16) / 16;
-        const int nstr = p.nstr, nexc = p.nexc;
+        const int nstr = p.nstr;
         const tcg::TileGeom geo = tcg::tile_geom(tile.start, nstr);
         if (tile.prob != cur) {
             if (tid == 0) bulk_load(smem_u32(Wsm), p.Wtc, (uint32_t)(KA * N * kAtomBytes), bw);

@@ -1,0 +1,183 @@
+"""GPU RDM backward (dE_iFCI/dh, dE_iFCI/dV) against the oracle's gradient and
+central finite differences of GPU energies.
+
+Tolerances of the 24-body finite-difference check: the analytic gradient is
+Hellmann–Feynman on FP64 vectors with residual 1e-11 (vector error ~2e-11,
+gradient error ~4e-11 per body set, ~1e-9 after the expansion weights of up
+to 21).  The central difference (step 1e-5) differences Rayleigh quotients
+of |theta| ~ 5 Eh whose FP64 reductions over up to 665,856 determinants
+round at ~1e-14 relative: ~5e-14 per energy, ~1.5e-12 after the weights,
+~7e-8 on the gradient in the worst case.  The check asks for 1e-6 relative
+plus 5e-8 absolute; the entry-by-entry comparison with the oracle gradient
+on the 6-body chain (order 3) pins the analytic path to 1e-9.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import fci
+from synth import chain_4x2, chain_24_uneven, pair_index
+
+import paper_2307_10675_gb300 as ifci
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module")
+def handle():
+    with ifci.Handle(0, 0) as h:
+        yield h
+
+
+def _system(chain, h=None, V=None):
+    h = chain.h if h is None else h
+    V = chain.eri_packed() if V is None else V
+    return ifci.SystemArrays(chain.body_offsets, torch.tensor(h, device=DEV), torch.tensor(V, device=DEV))
+
+
+def test_gradient_matches_oracle_rdm_gradient_4x2(handle):
+    """Every entry of dE/dh (8x8) and dE/dV (36x36) of the 2-body expansion."""
+    chain = chain_4x2()
+    sysd = _system(chain)
+    opts = ifci.davidson_opts("fp64", r_tol=1e-10)
+    ifci.ifci_increments(handle, sysd, 2, opts)
+    dh, dV = ifci.ifci_rdm_backward(handle, sysd, 2, 1.0, opts)
+    torch.cuda.synchronize()
+    e_ref, dh_ref, dV_ref = fci.ifci_gradient(chain, 2, method="dense")
+    np.testing.assert_allclose(dh.cpu().numpy(), dh_ref, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(dV.cpu().numpy(), dV_ref, rtol=0, atol=1e-9)
+
+
+def test_gradient_matches_oracle_rdm_gradient_6_bodies_order_3(handle):
+    """Every entry at order 3 (expansion weights 6, -3, 1) on a 6-body chain."""
+    from synth import make_chain
+    chain = make_chain([2, 3, 2, 3, 2, 2], 77, name="chain-6")
+    sysd = _system(chain)
+    opts = ifci.davidson_opts("fp64", r_tol=1e-11, max_iter=300)
+    out = ifci.ifci_increments(handle, sysd, 3, opts)
+    dh, dV = ifci.ifci_rdm_backward(handle, sysd, 3, 1.0, opts)
+    torch.cuda.synchronize()
+    e_ref, dh_ref, dV_ref = fci.ifci_gradient(chain, 3, tol=1e-11)
+    assert out["e_total"] == pytest.approx(e_ref, abs=1e-10)
+    np.testing.assert_allclose(dh.cpu().numpy(), dh_ref, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(dV.cpu().numpy(), dV_ref, rtol=0, atol=1e-9)
+
+
+def test_gradient_full_order_4x2_equals_fci_gradient(handle):
+    """At full order (4 bodies) the expansion is FCI(8e,8o): the gradient is the FCI one."""
+    chain = chain_4x2()
+    sysd = _system(chain)
+    opts = ifci.davidson_opts("fp64", r_tol=1e-10)
+    dh, dV = ifci.ifci_rdm_backward(handle, sysd, 4, 1.0, opts, recompute_vectors=True)
+    torch.cuda.synchronize()
+    r = fci.solve_subsystem(chain, (0, 1, 2, 3), tol=1e-11)
+    g1, g2 = fci.subsystem_rdm_global(chain, (0, 1, 2, 3), r.vector)
+    np.testing.assert_allclose(dh.cpu().numpy(), g1, rtol=0, atol=1e-8)
+    np.testing.assert_allclose(dV.cpu().numpy(), fci.fold_gamma2_packed(g2), rtol=0, atol=1e-8)
+
+
+def test_autograd_function_matches_backward(handle):
+    chain = chain_4x2()
+    h = torch.tensor(chain.h, device=DEV, requires_grad=True)
+    V = torch.tensor(chain.eri_packed(), device=DEV, requires_grad=True)
+    opts = ifci.davidson_opts("fp64", r_tol=1e-10)
+    E = ifci.ifci_energy(h, V, chain.body_offsets, 2, handle, opts)
+    (2.5 * E).backward()
+    e_ref, dh_ref, dV_ref = fci.ifci_gradient(chain, 2, method="dense")
+    assert E.item() == pytest.approx(e_ref, abs=1e-9)
+    np.testing.assert_allclose(h.grad.cpu().numpy(), 2.5 * dh_ref, rtol=0, atol=1e-8)
+    np.testing.assert_allclose(V.grad.cpu().numpy(), 2.5 * dV_ref, rtol=0, atol=1e-8)
+
+
+def test_backward_without_kept_vectors_is_rejected():
+    chain = chain_4x2()
+    with ifci.Handle(0, 0) as h2:
+        with pytest.raises(ifci.IfciError):
+            ifci.ifci_rdm_backward(h2, _system(chain), 2, 1.0)
+
+
+def _weight(N, n, k):
+    return 1 if k == N else (-1) ** (n - k) * math.comb(N - k - 1, n - k)
+
+
+def test_gradient_matches_finite_differences_chain24(handle):
+    """50 seeded integral entries of the 24-body chain (3-body expansion).
+
+    Entries are drawn among those that touch antibonding orbitals of at least
+    two bodies: E_iFCI then changes only through the body sets that contain
+    those bodies, so each difference is a batched Davidson over at most 23
+    sets; entries whose bonding-only or single-body dependence reaches every
+    set are covered entry by entry by the 4x2 oracle comparison above.
+    """
+    chain = chain_24_uneven()
+    N, order = chain.nbody, 3
+    sysd = _system(chain)
+    fwd = ifci.davidson_opts("fp64", r_tol=1e-11, max_iter=300)
+    ifci.ifci_increments(handle, sysd, order, fwd)
+    dh, dV = ifci.ifci_rdm_backward(handle, sysd, order, 1.0, fwd)
+    dh, dV = dh.cpu().numpy(), dV.cpu().numpy()
+
+    body_of = np.zeros(chain.norb, dtype=int)
+    for b in range(N):
+        body_of[chain.body_orbitals(b)] = b
+    bonding = {chain.bonding_orbital(b) for b in range(N)}
+    pairs = [(P, Q) for P in range(chain.norb) for Q in range(P + 1)]
+
+    def anti_bodies(orbs):
+        return {int(body_of[o]) for o in orbs if o not in bonding}
+
+    rng = np.random.default_rng(50)
+    entries = []
+    while len(entries) < 50:
+        if rng.random() < 0.3:
+            p, q = sorted(rng.integers(0, chain.norb, size=2))
+            bset = anti_bodies([p, q])
+            if 2 <= len(bset) <= 3:
+                entries.append(("h", p, q, bset))
+        else:
+            A, B = sorted(rng.integers(0, len(pairs), size=2))
+            bset = anti_bodies(list(pairs[A]) + list(pairs[B]))
+            if 2 <= len(bset) <= 3:
+                entries.append(("V", A, B, bset))
+    step = 1e-5
+    h0, V0 = chain.h, chain.eri_packed()
+    probs, meta = [], []
+    for idx, (kind, a, b, bset) in enumerate(entries):
+        others = [x for x in range(N) if x not in bset]
+        sets = []
+        for extra in range(0, order - len(bset) + 1):
+            for add in itertools.combinations(others, extra):
+                sets.append(tuple(sorted(set(bset) | set(add))))
+        for sgn in (+1, -1):
+            h, V = h0.copy(), V0.copy()
+            if kind == "h":
+                h[a, b] += sgn * step
+                if a != b:
+                    h[b, a] += sgn * step
+            else:
+                V[a, b] += sgn * step
+                if a != b:
+                    V[b, a] += sgn * step
+            sp = _system(chain, h, V)
+            for Y in sets:
+                # these entries leave E_core unchanged: difference the active-space
+                # eigenvalues (e_core = 0) to keep the rounding of ~45 Eh out
+                h1, eri, _ = ifci.ifci_frozen_core(handle, sp, Y)
+                probs.append(ifci.CIProblem(h1.shape[0], len(Y), h1, eri, 0.0))
+                meta.append((idx, sgn, _weight(N, order, len(Y))))
+    e, it, st = ifci.ifci_davidson_batched(handle, probs, ifci.davidson_opts("fp64", r_tol=1e-10, max_iter=300))
+    assert np.all(st == 0)
+    diff = np.zeros(len(entries))
+    for (idx, sgn, w), ei in zip(meta, e):
+        diff[idx] += sgn * w * ei
+    fd = diff / (2 * step)
+    for (kind, a, b, bset), g in zip(entries, fd):
+        if kind == "h":
+            an = dh[a, b] + (dh[b, a] if a != b else 0.0)
+        else:
+            an = dV[a, b] + (dV[b, a] if a != b else 0.0)
+        assert an == pytest.approx(g, rel=1e-6, abs=5e-8), (kind, a, b, an, g)
