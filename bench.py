@@ -7,6 +7,10 @@ largest CAS(6e,18o) with 665,856 determinants), frozen-body Hamiltonians,
 batched Davidson to convergence, and the FP64 increments with their sum,
 all through ``ifci_increments`` with device-resident integrals.
 
+Default path ("fp64e"): every sigma contraction FP64-accurate on BF16 tensor
+cores, all Davidson arithmetic FP64.  The same run also times the plain FP64
+path and the mixed BF16 path once each (``other_paths``) on the same GPU.
+
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 a bounded sample of the same workload instead.
 """
@@ -36,11 +40,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16", "fp64e"])
+    ap.add_argument("--precision", default="fp64e", choices=["fp64", "fp32", "bf16", "fp64e"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 and mixed comparison runs")
     ap.add_argument("--max-order", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sample-seconds", type=float, default=20.0)
+    ap.add_argument("--det-budget", type=int, default=0,
+                    help="determinants per sigma wave (0: library default)")
     return ap.parse_args()
 
 
@@ -206,79 +213,95 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    steps = args.steps if args.steps is not None else (1 if args.precision == "fp64" else 5)
+    steps = args.steps if args.steps is not None else (1 if args.precision == "fp64" else 3)
     warmup = max(3, args.warmup)
 
     chain = workload(rank)
     sysd = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=dev),
                              torch.tensor(chain.eri_packed(), device=dev))
-    opts = ifci.davidson_opts(args.precision, r_tol=1e-6, e_tol=1e-10)
     subs = subset_sizes(chain, args.max_order)
     nsub = len(subs)
     handle = ifci.Handle(0, local)
-    stream = torch.cuda.current_stream(dev)
 
-    for _ in range(warmup):
-        out = ifci.ifci_increments(handle, sysd, args.max_order, opts)
-    torch.cuda.synchronize(dev)
+    def opts_for(prec):
+        return ifci.davidson_opts(prec, r_tol=1e-6, e_tol=1e-10, max_iter=200, det_budget=args.det_budget)
 
-    handle.profile_enable(True)
-    l0 = handle.launches()
+    def timed(prec, nsteps, nwarm, profile=False):
+        for _ in range(nwarm):
+            ifci.ifci_increments(handle, sysd, args.max_order, opts_for(prec))
+        torch.cuda.synchronize(dev)
+        if profile:
+            handle.profile_enable(True)
+        l0 = handle.launches()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        stream = torch.cuda.current_stream(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(nsteps):
+            out = ifci.ifci_increments(handle, sysd, args.max_order, opts_for(prec))
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1)
+        prof = handle.profile_read() if profile else None
+        if profile:
+            handle.profile_enable(False)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return out, ms / nsteps, prof, handle.launches() - l0
+
     clocks = ClockSampler(local)
+    for _ in range(warmup):
+        ifci.ifci_increments(handle, sysd, args.max_order, opts_for(args.precision))
     clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(steps):
-        out = ifci.ifci_increments(handle, sysd, args.max_order, opts)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    if dist:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1)
+    out, ms_step, prof, launches = timed(args.precision, steps, 0, profile=True)
     clk = clocks.stop()
-    launches = handle.launches() - l0
-    prof = handle.profile_read()
-    handle.profile_enable(False)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    value = world * nsub / (ms_step / 1000.0)
 
     # algorithmic sigma FLOPs of a step: sigma builds per problem x 2 ndet npair^2
     its = out["iters"]
     flops_step = 0.0
+    exec_step = 0.0
     for (X, n, k), it in zip(subs, its):
-        flops_step += it * cost_of(n, k)[1]
-
-    ms_step = ms / steps
-    value = world * nsub / (ms_step / 1000.0)
-    c_ms, c_n = prof["contract"]
-    sig_ms = prof["gather"][0] + prof["contract"][0] + prof["scatter"][0]
-    flops_per_launch = flops_step * steps / max(1, c_n)
-    achieved_tf = flops_step * steps / (c_ms / 1000.0) / 1e12 if c_ms > 0 else None
-
+        nd, fl = cost_of(n, k)
+        flops_step += it * fl
+        exec_step += it * executed_oz_flops(n, k)
+    sig_ms = sum(prof[k][0] for k in ("gather", "contract", "contract_hi", "scatter")) / steps
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
+    bf = peaks.get("bf16_tflops_sustained")
+    bf_src = "MEASURED_PEAKS.json bf16_tflops_sustained" if bf else "fallback 1700 TFLOP/s (sustained)"
+    bf = bf or 1700.0
     if args.precision == "fp64":
+        c_ms = prof["contract"][0] / steps
         fp64_peak, fp64_how = _dgemm_peak(dev)
-        roof = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": (achieved_tf / fp64_peak) if (achieved_tf and fp64_peak) else None, "traffic": None,
-                "kernel": "contract_simt_kernel<double>", "peak_source": fp64_how,
-                "flops_per_launch": flops_per_launch}
+        ach = flops_step / (c_ms / 1000.0) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                "traffic": None, "kernel": "contract_simt_kernel<double>", "peak_source": fp64_how}
         dtype = "f64"
+    elif args.precision == "fp64e":
+        c_ms = prof["contract_hi"][0] / steps
+        ach = flops_step / (c_ms / 1000.0) / 1e12
+        pk = bf / 15.0
+        roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "traffic": None, "kernel": "oz_contract_kernel",
+                "peak_source": bf_src + " / 15 (15 BF16 slice products per FP64-accurate product)",
+                "executed_bf16_tflops": exec_step / (c_ms / 1000.0) / 1e12}
+        dtype = "f64 (BF16 tensor-core emulation)"
     else:
-        bf = peaks.get("bf16_tflops_sustained", 1700.0)
-        ratio = {"bf16": 1.0, "fp64e": 1.0, "tf32": 0.5, "fp32": 1.0 / 28.0}[args.precision]
-        pk = bf * ratio
-        roof = {"bound": "tensor", "achieved": achieved_tf, "peak": pk, "unit": "TFLOP/s",
-                "frac": (achieved_tf / pk) if achieved_tf else None, "traffic": None,
-                "peak_source": "MEASURED_PEAKS bf16 sustained x nominal dtype ratio"}
+        lo_ms = prof["contract"][0] / steps
+        hi_ms = prof["contract_hi"][0] / steps
+        ach = flops_step / ((lo_ms + hi_ms) / 1000.0) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": bf, "unit": "TFLOP/s", "frac": ach / bf,
+                "traffic": None, "kernel": "tc_contract_bf16_kernel + oz_contract_kernel", "peak_source": bf_src}
         dtype = args.precision + "+f64"
 
     line = {
@@ -291,16 +314,28 @@ def main():
                    "davidson": {"r_tol": 1e-6, "e_tol": 1e-10, "max_space": 12},
                    "l2": "inputs larger than L2: Davidson vectors of one step ~38 GB",
                    "parallelism": f"{world} independent chains (one per GPU)"},
-        "sigma_tflops": (flops_step * steps / (sig_ms / 1000.0) / 1e12) if sig_ms > 0 else None,
-        "kernel_ms": {k: v[0] / steps for k, v in prof.items()},
+        "sigma_tflops": flops_step / (sig_ms / 1000.0) / 1e12 if sig_ms > 0 else None,
+        "kernel_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
         "roofline": roof,
         "gpu_launches": int(launches),
         "clocks": clk,
         "e_total": out["e_total"],
     }
-
+    if not args.no_compare and world == 1:
+        paths = {}
+        if args.precision != "fp64":
+            o64, ms64, _, _ = timed("fp64", 1, 0)
+            paths["fp64"] = {"value": nsub / (ms64 / 1000.0), "ms_per_step": ms64, "warmup": 0,
+                             "e_total": o64["e_total"]}
+            line["speedup_vs_fp64_path"] = value / paths["fp64"]["value"]
+            line["e_total_minus_fp64_path"] = out["e_total"] - o64["e_total"]
+        if args.precision != "bf16":
+            ob, msb, _, _ = timed("bf16", 1, 1)
+            paths["bf16_mixed"] = {"value": nsub / (msb / 1000.0), "ms_per_step": msb, "warmup": 1,
+                                   "e_total": ob["e_total"]}
+        line["other_paths"] = paths
     if not args.no_e2e:
-        line["e2e"] = _e2e(ifci, handle, chain, args.max_order, opts, world, nsub, dist, dev)
+        line["e2e"] = _e2e(ifci, handle, chain, args.max_order, opts_for(args.precision), world, nsub, dist, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_baseline(workload(0), args.max_order, args.sample_seconds)
     handle.close()
@@ -309,6 +344,24 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def executed_oz_flops(n: int, m: int) -> float:
+    """BF16 MMA FLOPs the FP64-emulating contraction issues for one sigma of one
+    problem: row-aligned tiles of 128 determinants x 96-pair output tiles x
+    npair rounded to 16, 15 slice products."""
+    nstr = math.comb(n, m)
+    np_ = n * (n + 1) // 2
+    if nstr >= 128:
+        tiles = nstr * ((nstr + 127) // 128)
+    else:
+        r = min(16, 128 // nstr)
+        tiles = (nstr + r - 1) // r
+    kpad = (np_ + 15) // 16 * 16
+    npad = 0
+    for n0 in range(0, np_, 96):
+        npad += (min(96, np_ - n0) + 15) // 16 * 16
+    return 15.0 * 2.0 * tiles * 128 * npad * kpad
 
 
 def _dgemm_peak(dev):

@@ -23,6 +23,7 @@ struct ifci_handle_s {
     std::string last_error;
     long long launches = 0;
     int *d_err = nullptr;        // device flag set by kernels whose bounded waits ran out
+    int *d_counter = nullptr;    // tile counter of the dynamically scheduled kernels (reset per launch)
     // vectors kept by ifci_increments for ifci_rdm_backward
     struct Kept {
         bool valid = false;

@@ -43,7 +43,7 @@ static void dav_layout(const std::vector<ProbSpec> &specs, const ifci_davidson_o
     }
     size_t n = specs.size();
     z.nclass = (int)cls.size();
-    long long budget = o.det_budget > 0 ? o.det_budget : (1ll << 28);
+    long long budget = o.det_budget > 0 ? o.det_budget : (1ll << 31);   // two 16 GB intermediates
     budget = std::max(budget, z.max_pd);
     budget = std::min(budget, std::max(z.sum_pd, z.max_pd));
     z.budget = budget;

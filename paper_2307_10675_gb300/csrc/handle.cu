@@ -117,15 +117,16 @@ int ifci_handle_create(ifci_handle_t *handle, size_t workspace_bytes, int device
     cudaGetDevice(&prev);
     cudaSetDevice(device);
     int st = IFCI_OK;
-    if (cudaMalloc(&h->d_err, 256) != cudaSuccess || cudaMemset(h->d_err, 0, 256) != cudaSuccess) {
+    if (cudaMalloc(&h->d_err, 256) != cudaSuccess || cudaMemset(h->d_err, 0, 256) != cudaSuccess ||
+        cudaMalloc(&h->d_counter, 256) != cudaSuccess || cudaMemset(h->d_counter, 0, 256) != cudaSuccess) {
         cudaGetLastError();
-        h->d_err = nullptr;
         st = IFCI_ERR_CUDA;
     }
     if (st == IFCI_OK && workspace_bytes) st = ifci::ws_reserve(h, workspace_bytes);
     cudaSetDevice(prev);
     if (st != IFCI_OK) {
         if (h->d_err) cudaFree(h->d_err);
+        if (h->d_counter) cudaFree(h->d_counter);
         if (h->ws) cudaFree(h->ws);
         delete h;
         return st;
@@ -145,6 +146,7 @@ int ifci_handle_destroy(ifci_handle_t h) {
     if (h->ws) cudaFree(h->ws);
     if (h->kept.vec) cudaFree(h->kept.vec);
     if (h->d_err) cudaFree(h->d_err);
+    if (h->d_counter) cudaFree(h->d_counter);
     cudaSetDevice(prev);
     delete h;
     return IFCI_OK;

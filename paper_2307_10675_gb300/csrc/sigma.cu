@@ -10,6 +10,8 @@
 // merge of the alpha and beta lists with no atomics, and sigma is a gather.
 // D and G are pair-major planes [A][K] so that the alpha parts (whole rows
 // c[J_alpha][:]) are read and written with consecutive K across a warp.
+#include <algorithm>
+
 #include "sigma.cuh"
 #include "tc_gather.cuh"
 
@@ -248,6 +250,13 @@ int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision
         plan.max_delems = std::max(plan.max_delems, w.delems);
         plan.waves.push_back(w);
     }
+    // dynamically scheduled tensor-core tiles: largest problems first (longest
+    // tiles start early), stable within a problem
+    for (const SigmaWave &wv : plan.waves)
+        std::stable_sort(plan.tctiles.begin() + wv.tc0, plan.tctiles.begin() + wv.tc0 + wv.ntc,
+                         [&](const WorkItem &x, const WorkItem &y) {
+                             return plan.probs[x.prob].np > plan.probs[y.prob].np;
+                         });
     return IFCI_OK;
 }
 

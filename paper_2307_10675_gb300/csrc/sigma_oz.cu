@@ -63,40 +63,22 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// The CTA's sequence of W stages: (tile t, atom a) over its active tiles.
-struct StageCursor {
-    int t, a;
-};
-
-__device__ __forceinline__ bool tile_active(const SigmaProb *probs, const WorkItem *tiles, int t) {
-    const SigmaProb &p = probs[tiles[t].prob];
-    return !(p.active && !*p.active);
-}
-
-// next stage after (t, a) within [t, t1), skipping inactive tiles; t = t1 when none
-__device__ __forceinline__ StageCursor next_stage(const SigmaProb *probs, const WorkItem *tiles, StageCursor c,
-                                                  int t1) {
-    const int KA = k_atoms(probs[tiles[c.t].prob].np);
-    if (c.a + 1 < KA) return StageCursor{c.t, c.a + 1};
-    int t = c.t + 1;
-    while (t < t1 && !tile_active(probs, tiles, t)) t++;
-    return StageCursor{t, 0};
-}
-
-__device__ __forceinline__ const uint8_t *stage_src(const SigmaProb *probs, const WorkItem *tiles, StageCursor c) {
-    const WorkItem tile = tiles[c.t];
+__device__ __forceinline__ const uint8_t *stage_src(const SigmaProb *probs, const WorkItem *tiles, int t, int a) {
+    const WorkItem tile = tiles[t];
     const SigmaProb &p = probs[tile.prob];
     const int KA = k_atoms(p.np), nt = tile.sub / kNT;
-    return (const uint8_t *)p.Woz + ((size_t)nt * KA + c.a) * kWStage;
+    return (const uint8_t *)p.Woz + ((size_t)nt * KA + a) * kWStage;
 }
 
 // G[A][K] (int64, fixed point 2^-45 Wscale dscale) for one tile of 128 determinants x 96 pairs.
 __global__ void __launch_bounds__(kThreads, 1)
 oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__ tiles, int ntile,
-                   const long long *__restrict__ Q, long long *__restrict__ G, int *__restrict__ err) {
+                   const long long *__restrict__ Q, long long *__restrict__ G, int *__restrict__ err,
+                   int *__restrict__ counter) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_w[2], bar_mma;
     __shared__ uint32_t tmem_slot;
+    __shared__ int s_tile, s_next;
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *Wsm0 = base;                   // two W stages: [slice i][kNT rows][128 B]
     uint8_t *Asm = base + 2 * kWStage;      // [slice j][128 rows][128 B]
@@ -121,16 +103,20 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
-    const int per = (ntile + gridDim.x - 1) / gridDim.x;
-    const int t0 = blockIdx.x * per, t1 = min(ntile, t0 + per);
+    // tiles are handed out by a global counter (dynamic load balance); the tile
+    // after the current one is claimed early so that its first W stage can be
+    // prefetched during the current tile's last atom
     uint32_t ph_m = 0;
     uint32_t g = 0;            // W stages consumed so far: buffer g & 1, phase (g >> 1) & 1
     bool ok = true;
-    int tfirst = t0;
-    while (tfirst < t1 && !tile_active(probs, tiles, tfirst)) tfirst++;
-    if (tid == 0 && tfirst < t1) bulk_load(smem_u32(Wsm0), stage_src(probs, tiles, StageCursor{tfirst, 0}),
-                                           (uint32_t)kWStage, bw0);
-    for (int t = tfirst; t < t1 && ok;) {
+    if (tid == 0) {
+        const int t = tcg::claim_tile(counter, probs, tiles, ntile);
+        s_tile = t;
+        if (t < ntile) bulk_load(smem_u32(Wsm0), stage_src(probs, tiles, t, 0), (uint32_t)kWStage, bw0);
+    }
+    __syncthreads();
+    for (int t = s_tile; t < ntile && ok;) {
+        if (tid == 0) s_next = tcg::claim_tile(counter, probs, tiles, ntile);
         const WorkItem tile = tiles[t];
         const SigmaProb &p = probs[tile.prob];
         const int np = p.np, KA = k_atoms(np), n0 = tile.sub;
@@ -157,10 +143,13 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
                 ph_m ^= 1;
             }
             // the A buffer and W buffer (g + 1) & 1 are free now: prefetch the next stage
-            const StageCursor nx = next_stage(probs, tiles, StageCursor{t, a}, t1);
-            if (tid == 0 && nx.t < t1)
-                bulk_load(smem_u32(Wsm0 + ((g + 1) & 1) * kWStage), stage_src(probs, tiles, nx), (uint32_t)kWStage,
-                          ((g + 1) & 1) ? bw1 : bw0);
+            // (thread 0 wrote s_next itself, so it needs no barrier to read it)
+            if (tid == 0) {
+                const int nt2 = a + 1 < KA ? t : s_next, na = a + 1 < KA ? a + 1 : 0;
+                if (nt2 < ntile)
+                    bulk_load(smem_u32(Wsm0 + ((g + 1) & 1) * kWStage), stage_src(probs, tiles, nt2, na),
+                              (uint32_t)kWStage, ((g + 1) & 1) ? bw1 : bw0);
+            }
             // ---- five digit slices of the block, two 16-byte chunks per slice
 #pragma unroll
             for (int half = 0; half < 2; half++) {
@@ -216,6 +205,8 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
             ph_m ^= 1;
         }
         if (!ok) break;
+        // read before the closing barrier: thread 0 overwrites s_next after it
+        const int t_next = s_next;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // ---- epilogue: the levels are exact integers below 2^24; combine them
         // in int64, G = sum_L acc_L 2^{8 (4 - L)}  (no FP64 arithmetic)
@@ -242,8 +233,7 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        t++;
-        while (t < t1 && !tile_active(probs, tiles, t)) t++;
+        t = t_next;
     }
     if (!ok && tid == 0) atomicExch(err, 1);
     // a prefetch may still be in flight after a timeout: wait for it (bounded)
@@ -345,7 +335,7 @@ int launch_oz_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &
     for (const SigmaProb &p : plan.probs)
         if (p.np > kMaxNpExact)
             return set_error(h, IFCI_ERR_UNSUPPORTED, "FP64E: npair %d > %d (exact level sums)", p.np, kMaxNpExact);
-    if (!h->d_err) return set_error(h, IFCI_ERR_INVALID_ARG, "FP64E: no error flag");
+    if (!h->d_err || !h->d_counter) return set_error(h, IFCI_ERR_INVALID_ARG, "FP64E: no error flag / counter");
     const size_t smem = 1024 + 2 * kWStage + kAStage;   // 205,824 B
     static bool configured = false;
     if (!configured) {
@@ -354,9 +344,10 @@ int launch_oz_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &
         configured = true;
     }
     const int grid = std::min(w.ntc, device_sm_count(h->device));
+    IFCI_CUDA_TRY(h, cudaMemsetAsync(h->d_counter, 0, sizeof(int), s));
     ProfScope ps(h, s, PK_CONTRACT_HI);
     oz_contract_kernel<<<grid, kThreads, smem, s>>>(plan.d_probs, plan.d_tctiles + w.tc0, w.ntc,
-                                                    (const long long *)Q, (long long *)G, h->d_err);
+                                                    (const long long *)Q, (long long *)G, h->d_err, h->d_counter);
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;
 }

@@ -30,10 +30,11 @@ constexpr int kBfThreads = 512;   // four threads per determinant row
 __global__ void __launch_bounds__(kBfThreads, 1)
 tc_contract_bf16_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__ tiles, int ntile,
                         size_t w_bytes_max, size_t a_bytes_max, const float *__restrict__ Q,
-                        float *__restrict__ G, int *__restrict__ err) {
+                        float *__restrict__ G, int *__restrict__ err, int *__restrict__ counter) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_w, bar_mma;
     __shared__ uint32_t tmem_slot;
+    __shared__ int s_tile, s_next;
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *Wsm = base;
     uint8_t *Asm = base + ((w_bytes_max + 1023) & ~(size_t)1023);
@@ -57,16 +58,18 @@ tc_contract_bf16_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__r
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
-    // contiguous tile range of this CTA
-    const int per = (ntile + gridDim.x - 1) / gridDim.x;
-    const int t0 = blockIdx.x * per, t1 = min(ntile, t0 + per);
+    // tiles are handed out by a global counter (dynamic load balance; the
+    // tiles of a problem are consecutive, so W is reloaded only when the
+    // claimed tile belongs to another problem)
     int cur = -1;
     uint32_t ph_w = 0, ph_m = 0;
     bool ok = true;
-    for (int t = t0; t < t1 && ok; t++) {
+    if (tid == 0) s_tile = tcg::claim_tile(counter, probs, tiles, ntile);
+    __syncthreads();
+    for (int t = s_tile; t < ntile && ok;) {
+        if (tid == 0) s_next = tcg::claim_tile(counter, probs, tiles, ntile);
         const WorkItem tile = tiles[t];
         const SigmaProb &p = probs[tile.prob];
-        if (p.active && !*p.active) continue;
         const int np = p.np, N = n_pad(np), KA = k_atoms(np), KS = round_up(np, 16) / 16;
         const int nstr = p.nstr;
         const tcg::TileGeom geo = tcg::tile_geom(tile.start, nstr);
@@ -117,6 +120,8 @@ tc_contract_bf16_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__r
         __syncwarp();
         if (!__syncthreads_and(mbar_wait(bm, ph_m))) { ok = false; break; }
         ph_m ^= 1;
+        // read before the closing barrier: thread 0 overwrites s_next after it
+        const int t_next = s_next;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // ---- epilogue: TMEM -> G[A][K]; warps sharing a TMEM lane quarter split the columns
         float *Gp = G + p.doff;
@@ -133,6 +138,7 @@ tc_contract_bf16_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__r
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
+        t = t_next;
     }
     if (!ok && tid == 0) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -201,10 +207,12 @@ int launch_tc_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &
                                               (int)smem));
         configured_smem = (int)smem;
     }
+    if (!h->d_counter) return set_error(h, IFCI_ERR_INVALID_ARG, "tensor-core path: no tile counter");
     const int grid = std::min(w.ntc, device_sm_count(h->device));
+    IFCI_CUDA_TRY(h, cudaMemsetAsync(h->d_counter, 0, sizeof(int), s));
     ProfScope ps(h, s, PK_CONTRACT);
     tc_contract_bf16_kernel<<<grid, kBfThreads, smem, s>>>(plan.d_probs, plan.d_tctiles + w.tc0, w.ntc, wmax, amax,
-                                                    (const float *)D, (float *)G, h->d_err);
+                                                    (const float *)D, (float *)G, h->d_err, h->d_counter);
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;
 }

@@ -53,6 +53,18 @@ inline void append_row_tiles(std::vector<WorkItem> &out, int prob, int sub, int 
     }
 }
 
+// Dynamic tile scheduling of the persistent tensor-core kernels: the next tile
+// whose problem is still active, from a global counter (ntile when none is
+// left).  Called by one thread.
+__device__ __forceinline__ int claim_tile(int *counter, const SigmaProb *probs, const WorkItem *tiles, int ntile) {
+    while (true) {
+        const int t = atomicAdd(counter, 1);
+        if (t >= ntile) return ntile;
+        const SigmaProb &p = probs[tiles[t].prob];
+        if (!(p.active && !*p.active)) return t;
+    }
+}
+
 inline long long row_tile_count(int nstr) {
     if (nstr >= kTileDets) return (long long)nstr * ((nstr + kTileDets - 1) / kTileDets);
     int rmax = kTileDets / nstr;
