@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--sample-seconds", type=float, default=20.0)
     ap.add_argument("--det-budget", type=int, default=0,
                     help="determinants per sigma wave (0: library default)")
+    ap.add_argument("--case", default="increments", choices=["increments", "sigma"],
+                    help="sigma: time ifci_sigma alone on the workload's largest problem, CAS(6e,18o) "
+                         "(the small case for kernel profiles)")
     return ap.parse_args()
 
 
@@ -207,6 +210,9 @@ def main():
     import torch
     import paper_2307_10675_gb300 as ifci
 
+    if args.case == "sigma":
+        return sigma_case(args, torch, ifci)
+
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -343,6 +349,57 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+    return 0
+
+
+def sigma_case(args, torch, ifci):
+    """One sigma = H c of the workload's largest CI problem (three 6-orbital
+    bodies: CAS(6e,18o), 665,856 determinants, 171 pairs) on a spin-flip
+    symmetric vector, repeated; the kernel-level small case.  Prints one JSON
+    line with the per-call time."""
+    from synth import chain_24_uneven, random_ci_vector
+    dev = torch.device("cuda", 0)
+    chain = chain_24_uneven()
+    sysd = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=dev),
+                             torch.tensor(chain.eri_packed(), device=dev))
+    X = tuple(b for b, sz in enumerate(chain.body_sizes) if sz == 6)[:3]
+    n, m = 18, 3
+    steps = args.steps if args.steps is not None else 20
+    prec = ifci.PRECISIONS[args.precision]
+    with ifci.Handle(0, 0) as h:
+        h1, eri, _ = ifci.ifci_frozen_core(h, sysd, X)
+        t = ifci.ifci_build_strings(h, n, m)
+        nstr = math.comb(n, m)
+        c = torch.tensor(random_ci_vector(nstr, nstr, seed=1), device=dev).reshape(nstr, nstr)
+        c = (c + c.T).reshape(-1).contiguous()     # spin-flip symmetric, as every Davidson vector
+        c /= c.norm()
+        for _ in range(max(3, args.warmup)):
+            ifci.ifci_sigma(h, t, h1, eri, c, precision=prec, spin_symmetric=True)
+        torch.cuda.synchronize(dev)
+        h.profile_enable(True)
+        l0 = h.launches()
+        stream = torch.cuda.current_stream(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            ifci.ifci_sigma(h, t, h1, eri, c, precision=prec, spin_symmetric=True)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        prof = h.profile_read()
+        h.profile_enable(False)
+        launches = h.launches() - l0
+    ms = ev0.elapsed_time(ev1) / steps
+    nd, fl = cost_of(n, m)
+    line = {"case": "sigma", "workload": "CAS(6e,18o) of chain-24-uneven (bodies %s), 665,856 determinants" % (X,),
+            "precision": args.precision, "steps": steps, "ms_per_sigma": ms,
+            "algorithmic_tflops": fl / (ms / 1000.0) / 1e12,
+            "kernel_ms_per_sigma": {k: v[0] / steps for k, v in prof.items()},
+            "gpu_launches": int(launches)}
+    if args.precision == "fp64e":
+        c_ms = prof["contract_hi"][0] / steps
+        line["contract_hi_tflops_algorithmic"] = fl / (c_ms / 1000.0) / 1e12
+        line["contract_hi_executed_bf16_tflops"] = executed_oz_flops(n, m) / (c_ms / 1000.0) / 1e12
+    print(json.dumps(line), flush=True)
     return 0
 
 

@@ -59,11 +59,21 @@ typedef enum {
     IFCI_FP32 = 1, /* sigma contraction with FP32 inputs, FP32 accumulation */
     IFCI_TF32 = 2, /* sigma contraction on tensor cores, TF32 inputs, FP32 accumulation */
     IFCI_BF16 = 3, /* sigma contraction on tensor cores, BF16 inputs, FP32 accumulation */
-    IFCI_FP64E = 4 /* sigma contraction to ~FP64 accuracy on BF16 tensor cores: both
+    IFCI_FP64E = 4 /* sigma contraction to ~FP64 accuracy on FP16 tensor cores: both
                       operands split into 5 slices of 8-bit integers, the 15 leading
                       slice products accumulated exactly in FP32 per scale level,
-                      levels combined in FP64 (relative error ~2^-38 of max|W||D|) */
+                      levels combined in int64 (relative error ~2^-38 of max|W||D|) */
 } ifci_precision_t;
+
+/* Flag OR-ed into ifci_sigma's precision: the caller asserts that c is
+ * spin-flip symmetric, c[Ia][Ib] = c[Ib][Ia] (the singlet sector the Davidson
+ * solver works in).  The tensor-core precisions (BF16, FP64E) then gather the
+ * alpha excitations only and return S + S^T, S the sigma of the alpha-only
+ * intermediate, which equals H c for such c (a restatement of the sigma
+ * build, not a step of the paper).  Ignored by FP64 and FP32, and by
+ * spaces with 2 nstr^2 >= 2^31.  For a c that is not symmetric the result is
+ * not H c: do not set the flag there. */
+#define IFCI_SIGMA_SPIN_SYMMETRIC 0x100
 
 typedef struct ifci_handle_s *ifci_handle_t;
 

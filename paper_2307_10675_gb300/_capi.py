@@ -21,6 +21,7 @@ IFCI_ERR_TIMEOUT = 5
 IFCI_ERR_UNSUPPORTED = 6
 
 IFCI_FP64, IFCI_FP32, IFCI_TF32, IFCI_BF16, IFCI_FP64E = 0, 1, 2, 3, 4
+IFCI_SIGMA_SPIN_SYMMETRIC = 0x100
 
 EXPORTS = [
     "ifci_handle_create", "ifci_handle_destroy", "ifci_last_error_string", "ifci_workspace_bytes",

@@ -139,11 +139,15 @@ def ifci_build_strings(handle: Handle, norb: int, nelec_spin: int, stream=None, 
 # ---------------------------------------------------------------- one CI space
 
 def ifci_sigma(handle: Handle, tables: StringTables, h1: torch.Tensor, eri: torch.Tensor, c: torch.Tensor,
-               sigma: Optional[torch.Tensor] = None, precision: int = IFCI_FP64, stream=None) -> torch.Tensor:
+               sigma: Optional[torch.Tensor] = None, precision: int = IFCI_FP64, stream=None,
+               spin_symmetric: bool = False) -> torch.Tensor:
+    """sigma = H c.  ``spin_symmetric``: the caller asserts c[Ia][Ib] = c[Ib][Ia];
+    the tensor-core precisions then take the alpha-only gather."""
     if sigma is None:
         sigma = torch.empty_like(c)
+    prec = int(precision) | (_capi.IFCI_SIGMA_SPIN_SYMMETRIC if spin_symmetric else 0)
     handle.check(_lib().ifci_sigma(handle.ptr, tables.as_c(), _ptr(h1), _ptr(eri), _ptr(c), _ptr(sigma),
-                                   int(precision), _stream(stream)))
+                                   prec, _stream(stream)))
     return sigma
 
 

@@ -22,6 +22,8 @@ int ifci_sigma(ifci_handle_t h, const ifci_strings_t *str, const double *h1, con
         return set_error(h, IFCI_ERR_INVALID_ARG, "ifci_sigma: inconsistent string table (norb=%d nelec=%d)",
                          str->norb, str->nelec_spin);
     if (c == sigma) return set_error(h, IFCI_ERR_INVALID_ARG, "ifci_sigma: sigma aliases c");
+    const bool sym_req = (precision & IFCI_SIGMA_SPIN_SYMMETRIC) != 0;
+    precision &= ~IFCI_SIGMA_SPIN_SYMMETRIC;
     if (precision < IFCI_FP64 || precision > IFCI_FP64E)
         return set_error(h, IFCI_ERR_INVALID_ARG, "ifci_sigma: precision %d", precision);
     const bool tc = precision == IFCI_BF16 || precision == IFCI_TF32;
@@ -38,13 +40,16 @@ int ifci_sigma(ifci_handle_t h, const ifci_strings_t *str, const double *h1, con
     p.n = n; p.nstr = nstr; p.nexc = nexc; p.np = np; p.ld = ld;
     p.ndet = ndet; p.stride = ndet; p.exc = str->exc;
     p.cbase = c; p.sbase = sigma;
+    const bool sym = sym_req && (tc || oz) && 2 * ndet < (1ll << 31);
+    p.sym = sym ? 1 : 0;   // the pair map is placed below, before the plan is uploaded
     plan.probs.push_back(p);
-    IFCI_TRY(plan_sigma(h, plan, (long long)np * ndet, precision));
+    IFCI_TRY(plan_sigma(h, plan, sigma_elems(np, ndet), precision));
     const size_t eb = sigma_elem_bytes(precision);
     size_t need = ws_round(sizeof(FoldDesc)) + ws_round((size_t)ld * ld * 8) + ws_round((size_t)ld * ld * 4) +
                   (tc ? ws_round((size_t)tc_operand_bytes(np, precision)) : 0) +
                   (oz ? ws_round((size_t)oz_operand_bytes(np)) + ws_round(8) : 0) +
-                  ((tc || oz) ? ws_round((size_t)nstr * kBlk16Stride) : 0) + plan_device_bytes(plan) +
+                  ((tc || oz) ? ws_round((size_t)nstr * kBlk16Stride) : 0) +
+                  (sym ? ws_round((size_t)nstr * pmap_ld(np) * 4) : 0) + plan_device_bytes(plan) +
                   2 * ws_round((size_t)plan.max_delems * eb);
     IFCI_TRY(ws_reserve(h, need));
     auto *fd = ws_take<FoldDesc>(h, 1);
@@ -60,10 +65,13 @@ int ifci_sigma(ifci_handle_t h, const ifci_strings_t *str, const double *h1, con
     plan.probs[0].dscale = 2.0;
     uint8_t *blk = (tc || oz) ? ws_take<uint8_t>(h, (size_t)nstr * kBlk16Stride) : nullptr;
     plan.probs[0].blk = blk;
+    int32_t *pmap = sym ? ws_take<int32_t>(h, (size_t)nstr * pmap_ld(np)) : nullptr;
+    plan.probs[0].pmap = pmap;
     FoldDesc f{n, 2 * str->nelec_spin, ld, h1, eri, W};
     IFCI_CUDA_TRY(h, cudaMemcpyAsync(fd, &f, sizeof(f), cudaMemcpyHostToDevice, s));
     IFCI_TRY(launch_fold(h, 1, fd, np, s));
     if (blk) IFCI_TRY(launch_exc_blocks(h, nstr, nexc, str->exc, blk, s));
+    if (pmap) IFCI_TRY(launch_pair_map(h, nstr, nexc, np, str->exc, pmap, s));
     IFCI_TRY(upload_plan(h, plan, s));
     if (precision == IFCI_FP32) IFCI_TRY(launch_convert_w(h, 1, plan.d_probs, s));
     if (tc) IFCI_TRY(launch_tc_pack_w(h, 1, plan.d_probs, precision, s));

@@ -116,5 +116,9 @@ inline cudaStream_t as_cuda(ifci_stream_t s) { return reinterpret_cast<cudaStrea
 
 int device_sm_count(int device);
 int launch_exc_blocks(ifci_handle_t h, int nstr, int nexc, const int32_t *exc, uint8_t *blk, cudaStream_t s);
+// row stride (int32 entries) of the dense pair map
+__host__ __device__ inline int pmap_ld(int np) { return (np + 15) / 16 * 16; }
+// pair map of the spin-flip-symmetric tensor-core gathers (needs 2 nstr^2 < 2^31)
+int launch_pair_map(ifci_handle_t h, int nstr, int nexc, int np, const int32_t *exc, int32_t *pmap, cudaStream_t s);
 
 }  // namespace ifci

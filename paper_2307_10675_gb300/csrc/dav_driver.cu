@@ -27,6 +27,7 @@ static void dav_layout(const std::vector<ProbSpec> &specs, const ifci_davidson_o
             cls[{p.n, p.m}] = (int)cls.size();
             z.bytes += ws_round((size_t)nstr * 8) + ws_round((size_t)nstr * nexc * 4) +
                        ws_round((size_t)nstr * kBlk16Stride);
+            if (tc || oz) z.bytes += ws_round((size_t)nstr * pmap_ld(np) * 4);   // pair map
         }
         z.bytes += ws_round((size_t)np * np * 8);                       // W
         if (lo) z.bytes += ws_round((size_t)np * np * 4);               // Wf
@@ -35,8 +36,8 @@ static void dav_layout(const std::vector<ProbSpec> &specs, const ifci_davidson_o
         z.bytes += ws_round((size_t)ndet * 8);                          // hd
         z.bytes += 2 * ws_round((size_t)(ms + 1) * ndet * 8);           // B, S
         z.nitem += (int)((ndet + kVecChunk - 1) / kVecChunk);
-        z.max_pd = std::max(z.max_pd, (long long)np * ndet);
-        z.sum_pd += (long long)np * ndet;
+        z.max_pd = std::max(z.max_pd, sigma_elems(np, ndet));
+        z.sum_pd += sigma_elems(np, ndet);
         z.n_items_sigma += (ndet + kGatherChunk - 1) / kGatherChunk;
         z.n_tiles_sigma += ((np + kGemmTM - 1) / kGemmTM) * ((ndet + kGemmTN - 1) / kGemmTN) +
                            tcg::row_tile_count(nstr) * ((np + oz_tile_n() - 1) / oz_tile_n() + 1);
@@ -103,6 +104,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
     // string tables per class
     std::map<std::pair<int, int>, std::pair<uint64_t *, int32_t *>> tables;
     std::map<std::pair<int, int>, uint8_t *> blocks;
+    std::map<std::pair<int, int>, int32_t *> pmaps;
     for (const ProbSpec &p : specs) {
         auto key = std::make_pair(p.n, p.m);
         if (tables.count(key)) continue;
@@ -118,6 +120,16 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
         if (!bl) return set_error(h, IFCI_ERR_OOM, "davidson: workspace (block table)");
         IFCI_TRY(launch_exc_blocks(h, nstr, nexc, ex, bl, s));
         blocks[key] = bl;
+        // Davidson vectors are spin-flip symmetric: the tensor-core sigmas use
+        // the alpha-only gathers where the pair map's offsets fit in int32
+        int32_t *pm = nullptr;
+        if ((tc || oz) && 2ll * nstr * nstr < (1ll << 31)) {
+            const int np = p.n * (p.n + 1) / 2;
+            pm = ws_take<int32_t>(h, (size_t)nstr * pmap_ld(np));
+            if (!pm) return set_error(h, IFCI_ERR_OOM, "davidson: workspace (pair map)");
+            IFCI_TRY(launch_pair_map(h, nstr, nexc, np, ex, pm, s));
+        }
+        pmaps[key] = pm;
     }
 
     DavBatch b;
@@ -170,6 +182,8 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
         sp.n = p.n; sp.nstr = nstr; sp.nexc = nexc; sp.np = np; sp.ld = np;
         sp.ndet = ndet; sp.stride = ndet; sp.exc = tb.second;
         sp.blk = blocks[{p.n, p.m}];
+        sp.pmap = pmaps[{p.n, p.m}];
+        sp.sym = sp.pmap ? 1 : 0;   // plan_sigma keeps it for the tensor-core plans only
         sp.W = W; sp.Wf = Wf; sp.Wtc = Wtc;
         sp.Woz = Woz;
         sp.Wexp = oz ? (double *)(Woz + (oz_operand_bytes(np) - np * 8 - 256)) : nullptr;

@@ -10,6 +10,15 @@
 // merge of the alpha and beta lists with no atomics, and sigma is a gather.
 // D and G are pair-major planes [A][K] so that the alpha parts (whole rows
 // c[J_alpha][:]) are read and written with consecutive K across a warp.
+//
+// Spin-flip-symmetric vectors (C = C^T, the singlet sector the Davidson
+// solver works in): with X_A the (symmetric) string matrix of E+_A, the beta
+// part of D is the transpose of the alpha part, D_beta[A] = C X_A = (X_A C)^T,
+// so G = G_a + G_a^T with G_a = W D_alpha, and
+//   sigma = sum_A X_A G[A] + G[A] X_A = S + S^T,  S = sum_A X_A G_a[A] + G_a[A] X_A.
+// The tensor-core paths then gather alpha excitations only (every thread of
+// a tile row shares one alpha list, read from a dense pair map), run the
+// unchanged scatter on G_a to get S, and add the transpose of S.
 #include <algorithm>
 
 #include "sigma.cuh"
@@ -157,12 +166,36 @@ quantise_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict_
     if (I >= p.ndet) return;
     const double *c = p.cbase + (p.cslot ? (long long)*p.cslot : 0ll) * p.stride;
     const long long off = p.qoff;
+    // symmetric gathers read the negated copy at off + ndet (sign by address)
     if (KIND == 0) {
-        reinterpret_cast<float *>(qbuf)[off + I] = (float)c[I];
+        const float v = (float)c[I];
+        reinterpret_cast<float *>(qbuf)[off + I] = v;
+        if (p.sym) reinterpret_cast<float *>(qbuf)[off + p.ndet + I] = -v;
     } else {
         const double sc = 274877906944.0 / p.dscale;   // 2^38 / dscale
-        reinterpret_cast<long long *>(qbuf)[off + I] = __double2ll_rn(c[I] * sc);
+        const long long v = __double2ll_rn(c[I] * sc);
+        reinterpret_cast<long long *>(qbuf)[off + I] = v;
+        if (p.sym) reinterpret_cast<long long *>(qbuf)[off + p.ndet + I] = -v;
     }
+}
+
+// sigma = S + S^T in place for the spin-flip-symmetric problems (each
+// unordered pair of determinants (ka, kb), (kb, ka) is owned by one thread).
+__global__ void __launch_bounds__(kGatherChunk)
+sym_sum_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__ items) {
+    const WorkItem it = items[blockIdx.x];
+    const SigmaProb &p = probs[it.prob];
+    if (!p.sym || (p.active && !*p.active)) return;
+    const long long K = it.start + threadIdx.x;
+    if (K >= p.ndet) return;
+    const int nstr = p.nstr;
+    const int ka = (int)(K / nstr), kb = (int)(K % nstr);
+    if (ka > kb) return;
+    double *s = p.sbase + (p.sslot ? (long long)*p.sslot : 0ll) * p.stride;
+    const long long T = (long long)kb * nstr + ka;
+    const double v = s[K] + s[T];
+    s[K] = v;
+    s[T] = v;
 }
 
 // Scatter of the FP64-emulating path: G is int64 fixed point with one scale
@@ -208,7 +241,9 @@ int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision
     SigmaWave w{0, 0, 0, 0, 0, 0, 0, 0};
     for (size_t i = 0; i < plan.probs.size(); i++) {
         SigmaProb &p = plan.probs[i];
-        long long need = (long long)p.np * p.ndet;
+        // the alpha-only form is a tensor-core gather; the CUDA-core paths build the full D
+        p.sym = (p.sym && (tc || precision == IFCI_FP64E) && 2 * p.ndet < (1ll << 31)) ? 1 : 0;
+        long long need = sigma_elems(p.np, p.ndet);
         if (need > budget)
             return set_error(h, IFCI_ERR_OOM, "sigma: one problem needs %lld intermediate elements, budget %lld",
                              need, budget);
@@ -220,7 +255,7 @@ int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision
         p.doff = w.delems;
         w.delems += need;
         p.qoff = w.qelems;
-        w.qelems += p.ndet;
+        w.qelems += p.sym ? 2 * p.ndet : p.ndet;
         for (long long s0 = 0; s0 < p.ndet; s0 += kGatherChunk) {
             plan.items.push_back(WorkItem{(int)i, 0, s0});
             w.nitem++;
@@ -250,6 +285,8 @@ int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision
         plan.max_delems = std::max(plan.max_delems, w.delems);
         plan.waves.push_back(w);
     }
+    plan.any_sym = false;
+    for (const SigmaProb &p : plan.probs) plan.any_sym = plan.any_sym || p.sym;
     // dynamically scheduled tensor-core tiles: largest problems first (longest
     // tiles start early), stable within a problem
     for (const SigmaWave &wv : plan.waves)
@@ -266,6 +303,8 @@ size_t plan_device_bytes(const SigmaPlan &plan) {
 }
 
 int upload_plan(ifci_handle_t h, SigmaPlan &plan, cudaStream_t s) {
+    for (const SigmaProb &p : plan.probs)
+        if (p.sym && !p.pmap) return set_error(h, IFCI_ERR_INVALID_ARG, "sigma plan: symmetric problem without pair map");
     plan.d_probs = ws_take<SigmaProb>(h, std::max<size_t>(1, plan.probs.size()));
     plan.d_items = ws_take<WorkItem>(h, std::max<size_t>(1, plan.items.size()));
     plan.d_tiles = ws_take<WorkItem>(h, std::max<size_t>(1, plan.tiles.size()));
@@ -334,6 +373,10 @@ int run_sigma(ifci_handle_t h, const SigmaPlan &plan, int precision, void *D, vo
             scatter_fixed_kernel<<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
                                                                   (const long long *)G);
             IFCI_LAUNCH_CHECK(h);
+            if (plan.any_sym) {
+                sym_sum_kernel<<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0);
+                IFCI_LAUNCH_CHECK(h);
+            }
         } else {
             {
                 ProfScope ps(h, s, PK_GATHER);
@@ -345,6 +388,10 @@ int run_sigma(ifci_handle_t h, const SigmaPlan &plan, int precision, void *D, vo
             scatter_kernel<float><<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
                                                                    (const float *)G);
             IFCI_LAUNCH_CHECK(h);
+            if (plan.any_sym) {
+                sym_sum_kernel<<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0);
+                IFCI_LAUNCH_CHECK(h);
+            }
         }
     }
     return IFCI_OK;

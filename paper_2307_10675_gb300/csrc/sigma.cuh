@@ -10,11 +10,13 @@ namespace ifci {
 struct SigmaProb {
     int n, nstr, nexc, np;   // active orbitals, strings, excitations per string, pairs
     int ld;                  // row stride of W (>= np)
-    int pad_;
+    int sym;                 // 1: the vector is spin-flip symmetric (C = C^T); the tensor-core paths gather
+                             // alpha excitations only and return S + S^T (set by plan_sigma, needs pmap)
     long long ndet;
     long long stride;
     const int32_t *exc;      // [nstr * nexc] excitation table of (n, nelec_spin)
     const uint8_t *blk;      // [nstr * kBlk16Stride] entry offsets per 16-pair block (tensor-core paths)
+    const int32_t *pmap;     // [nstr * pmap_ld(np)] dense pair map (spin-flip-symmetric gathers) or nullptr
     const double *W;         // [ld * ld] folded contraction matrix, FP64
     const float *Wf;         // [ld * ld] FP32 copy (FP32 path) or nullptr
     const void *Wtc;         // tensor-core operand image (BF16 path) or nullptr
@@ -29,6 +31,10 @@ struct SigmaProb {
     const int *active;       // device flag or nullptr (= active)
     long long doff;          // element offset of this problem's D and G blocks in a wave
 };
+
+// D/G elements one problem takes in a wave (the quantised +-c copies of the
+// symmetric tensor-core gathers share the D buffer and need 2 ndet)
+inline long long sigma_elems(int np, long long ndet) { return (long long)(np < 2 ? 2 : np) * ndet; }
 
 struct WorkItem {
     int prob;
@@ -53,6 +59,7 @@ struct SigmaPlan {
     std::vector<SigmaWave> waves;
     std::vector<WorkItem> items, tiles, tctiles;
     long long max_delems = 0;
+    bool any_sym = false;    // some problem uses the spin-flip-symmetric gathers
     SigmaProb *d_probs = nullptr;
     WorkItem *d_items = nullptr, *d_tiles = nullptr, *d_tctiles = nullptr;
 };

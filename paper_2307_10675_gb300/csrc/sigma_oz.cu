@@ -1,16 +1,17 @@
-// FP64-accurate contraction G = W D on BF16 tensor cores (tcgen05).
+// FP64-accurate contraction G = W D on the FP16 tensor cores (tcgen05).
 //
-// GB300 runs FP64 at ~1/1800 of its BF16 tensor rate, so the sigma builds
+// GB300 runs FP64 at ~1/1800 of its 16-bit tensor rate, so the sigma builds
 // that must be exact to FP64 level (Davidson restart vectors, final Rayleigh
 // quotients) are emulated with integer slices (an Ozaki-style splitting):
 //
 //   W[A][B] = Wscale 2^-7 (w1 + 2^-8 w2 + ... + 2^-32 w5)    Wscale >= max|W|
 //   D[B][K] = dscale  2^-6 (d1 + 2^-8 d2 + ... + 2^-32 d5)    dscale >= max|D|
 //
-// with every slice an integer in [-128, 128], exact in BF16.  D comes from the
+// with every slice an integer in [-128, 128], exact in FP16.  D comes from the
 // fixed-point copy round(c 2^38 / dscale) of the input vector (quantise_kernel),
 // so the gather adds integers and the slices are the base-256 digits of
-// X + 128 (1 + 2^8 + ... + 2^32) minus 128: no FP64 arithmetic in this kernel.
+// X + 128 (1 + 2^8 + ... + 2^32) minus 128, turned into FP16 by a byte permute
+// and one packed FP16 subtraction: no FP64 arithmetic in this kernel.
 // The product of two slices over K <= 204 terms stays below 2^24 even when the (up to five)
 // slice pairs of one scale level L = i + j share an accumulator, so each level
 // is summed exactly by the tensor cores in FP32.  The 15 slice pairs with
@@ -22,10 +23,14 @@
 //
 // Tile: 128 determinants (TMEM lanes) x 96 output pairs; five accumulators
 // of 96 FP32 columns (480 of the 512 TMEM columns).  K runs in 64-pair atoms:
-// the W slices of the next atom (5 x 96 x 64 BF16, pre-swizzled image) arrive
+// the W slices of the next atom (5 x 96 x 64 FP16, pre-swizzled image) arrive
 // by bulk async copy into the second stage buffer while 512 threads (four per
 // determinant) build the five D slices of the current atom, then one thread
-// issues the 15 x 4 MMAs.
+// issues the 15 x 4 MMAs.  For spin-flip-symmetric vectors the gather reads
+// the alpha excitations only (see sigma.cu): one pair-map lookup and one
+// predicated load per element.
+#include <cuda_fp16.h>
+
 #include "sigma.cuh"
 #include "tc_gather.cuh"
 #include "tcgen05.cuh"
@@ -59,8 +64,21 @@ __device__ __forceinline__ void slice5(double x, float (&sl)[kS]) {
 }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-    __nv_bfloat16 a = __float2bfloat16_rn(lo), b = __float2bfloat16_rn(hi);   // exact: |lo|, |hi| <= 128, integers
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+    __half a = __float2half_rn(lo), b = __float2half_rn(hi);   // exact: |lo|, |hi| <= 128, integers
+    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+// FP16 pair (u0 - 128, u1 - 128) of byte D of a and of b: the byte permute
+// puts u into the low mantissa bits of the FP16 number 1024 (0x6400), which
+// then reads 1024 + u exactly, and one packed subtraction of 1152 leaves
+// u - 128 in [-128, 127] (exact).
+__device__ __forceinline__ uint32_t digit_pair_f16(uint32_t a, uint32_t b, int D) {
+    const uint32_t sel = D | (D << 4) | ((D + 4) << 8) | ((D + 4) << 12);   // a compile-time constant once unrolled
+    const uint32_t t = (__byte_perm(a, b, sel) & 0x00FF00FFu) | 0x64006400u;
+    __half2 v = *reinterpret_cast<const __half2 *>(&t);
+    const __half2 off = __halves2half2(__ushort_as_half((unsigned short)0x6480), __ushort_as_half((unsigned short)0x6480));
+    v = __hsub2(v, off);
+    return *reinterpret_cast<uint32_t *>(&v);
 }
 
 __device__ __forceinline__ const uint8_t *stage_src(const SigmaProb *probs, const WorkItem *tiles, int t, int a) {
@@ -137,7 +155,10 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
             long long x[16];
 #pragma unroll
             for (int k = 0; k < 16; k++) x[k] = 0;
-            if (live) tcg::gather_block16<long long>(p, C, ka, kb, b, x);
+            if (live) {
+                if (p.sym) tcg::gather_alpha16<long long>(p, C, ka, kb, b, x);
+                else tcg::gather_block16<long long>(p, C, ka, kb, b, x);
+            }
             if (a > 0) {
                 if (!__syncthreads_and(mbar_wait(bm, ph_m))) { ok = false; break; }
                 ph_m ^= 1;
@@ -167,11 +188,8 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
                     const int d = kS - 1 - j;          // slice j = digit d (j = 0 most significant)
                     uint32_t w4[4];
 #pragma unroll
-                    for (int e = 0; e < 8; e += 2) {
-                        const uint32_t u0 = d == 4 ? (hi[e] & 255u) : ((lo[e] >> (8 * d)) & 255u);
-                        const uint32_t u1 = d == 4 ? (hi[e + 1] & 255u) : ((lo[e + 1] >> (8 * d)) & 255u);
-                        w4[e / 2] = pack_bf16x2f((float)((int)u0 - 128), (float)((int)u1 - 128));
-                    }
+                    for (int e = 0; e < 8; e += 2)
+                        w4[e / 2] = d == 4 ? digit_pair_f16(hi[e], hi[e + 1], 0) : digit_pair_f16(lo[e], lo[e + 1], d);
                     *(uint4 *)(dst + (size_t)j * kTM * kAtomBytes) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
                 }
             }
@@ -180,7 +198,7 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
             if (!__syncthreads_and(mbar_wait(bwg, (g >> 1) & 1))) { ok = false; break; }
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t idesc = idesc_bf16(kTM, Nt);
+                const uint32_t idesc = idesc_f16(kTM, Nt);
                 const uint32_t a0 = smem_u32(Asm), w0 = smem_u32(Wsm0 + (g & 1) * kWStage);
                 const int kst = min(4, (round_up(np, 16) - a * 64) / 16);
                 for (int j = 0; j < kS; j++) {
@@ -188,7 +206,7 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
                         const int L = i + j;
                         for (int ks = 0; ks < kst; ks++) {
                             const uint32_t acc = (started >> L) & 1u;
-                            mma_bf16(tmem + (uint32_t)(L * kNT),
+                            mma_f16(tmem + (uint32_t)(L * kNT),
                                      smem_desc(a0 + (uint32_t)(j * kTM * kAtomBytes + ks * 32)),
                                      smem_desc(w0 + (uint32_t)(i * kNT * kAtomBytes + ks * 32)), idesc, acc);
                             started |= 1u << L;

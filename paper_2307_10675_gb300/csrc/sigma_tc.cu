@@ -3,17 +3,18 @@
 //
 // One tile = 128 determinants (the MMA's M, one TMEM lane each) x all npair
 // output pairs (N <= 256 columns of FP32 in TMEM) x all npair input pairs (K).
-//   A (M x K, K-major, SWIZZLE_128B) : D^T rows, built in shared memory by the
-//       128 threads, one determinant each, from the sorted alpha/beta
-//       excitation lists (no atomics, one rounding per element)
+//   A (M x K, K-major, SWIZZLE_128B) : D^T rows, built in shared memory by
+//       512 threads, four per determinant, from the sorted alpha/beta
+//       excitation lists (no atomics, one rounding per element); for
+//       spin-flip-symmetric vectors from the alpha pair map only (sigma.cu)
 //   B (N x K, K-major, SWIZZLE_128B) : the folded integrals W of the
 //       problem, a pre-swizzled BF16 image copied with one bulk async copy
 //       (cp.async.bulk) whenever the CTA moves to a new problem
 //   D (M x N, FP32, TMEM)            : G^T of the tile; the epilogue reads it
 //       with tcgen05.ld (one determinant per thread) and stores G[A][K] so
 //       that a warp writes 32 consecutive determinants per pair.
-// CTAs are persistent and take contiguous tile ranges, so W is reloaded only
-// at problem boundaries.  Every mbarrier wait is bounded; on a timeout the
+// CTAs are persistent and claim tiles from a global counter; the tiles of a
+// problem are consecutive, so W is reloaded mostly at problem boundaries.  Every mbarrier wait is bounded; on a timeout the
 // kernel records an error flag, frees its TMEM and returns.
 #include "sigma.cuh"
 #include "tc_gather.cuh"
@@ -91,7 +92,10 @@ tc_contract_bf16_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__r
             float x[16];
 #pragma unroll
             for (int k = 0; k < 16; k++) x[k] = 0.0f;
-            if (live) tcg::gather_block16<float>(p, c, ka, kb, b, x);
+            if (live) {
+                if (p.sym) tcg::gather_alpha16<float>(p, c, ka, kb, b, x);
+                else tcg::gather_block16<float>(p, c, ka, kb, b, x);
+            }
 #pragma unroll
             for (int half = 0; half < 2; half++) {
                 const int ch = 2 * (b & 3) + half;   // chunk within the atom
@@ -113,7 +117,7 @@ tc_contract_bf16_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__r
                 const uint32_t koff = (uint32_t)((ks & 3) * 32);   // 16 BF16 = 32 B inside the atom
                 const uint32_t aaddr = a0 + (uint32_t)(ks >> 2) * (kTM * kAtomBytes) + koff;
                 const uint32_t baddr = b0 + (uint32_t)(ks >> 2) * (uint32_t)(N * kAtomBytes) + koff;
-                mma_bf16(tmem, smem_desc(aaddr), smem_desc(baddr), idesc, ks > 0 ? 1u : 0u);
+                mma_f16(tmem, smem_desc(aaddr), smem_desc(baddr), idesc, ks > 0 ? 1u : 0u);
             }
             mma_commit(bm);
         }

@@ -80,6 +80,32 @@ __global__ void exc_blocks_kernel(int nstr, int nexc, const int32_t *__restrict_
     }
 }
 
+// Dense pair map of a string table for spin-flip-symmetric vectors:
+// pmap[I][A] = J nstr + neg ndet for the entry (J, A, neg) of string I, -1 where
+// I has no excitation on pair A (rows padded to pmap_ld(np) with -1).  The
+// value is the element offset of +-c[J][0] in the pair [c | -c] of quantised
+// copies, so the tensor-core gathers pick the sign by address.
+__global__ void pair_map_kernel(int nstr, int nexc, int np, long long ndet, const int32_t *__restrict__ exc,
+                                int32_t *__restrict__ pmap) {
+    const int I = blockIdx.x;
+    const int ld = pmap_ld(np);
+    int32_t *row = pmap + (size_t)I * ld;
+    for (int A = threadIdx.x; A < ld; A += blockDim.x) row[A] = -1;
+    __syncthreads();
+    for (int e = threadIdx.x; e < nexc; e += blockDim.x) {
+        const int32_t x = exc[(size_t)I * nexc + e];
+        row[exc_pair(x)] = (int32_t)((long long)exc_J(x) * nstr + ((x & 1) ? ndet : 0));
+    }
+}
+
+int launch_pair_map(ifci_handle_t h, int nstr, int nexc, int np, const int32_t *exc, int32_t *pmap, cudaStream_t s) {
+    const long long ndet = (long long)nstr * nstr;
+    if (2 * ndet >= (1ll << 31)) return set_error(h, IFCI_ERR_INVALID_ARG, "pair map: %lld determinants", ndet);
+    pair_map_kernel<<<nstr, 128, 0, s>>>(nstr, nexc, np, ndet, exc, pmap);
+    IFCI_LAUNCH_CHECK(h);
+    return IFCI_OK;
+}
+
 int launch_exc_blocks(ifci_handle_t h, int nstr, int nexc, const int32_t *exc, uint8_t *blk, cudaStream_t s) {
     exc_blocks_kernel<<<(nstr + 127) / 128, 128, 0, s>>>(nstr, nexc, exc, blk);
     IFCI_LAUNCH_CHECK(h);

@@ -135,5 +135,28 @@ __device__ __forceinline__ void gather_block16(const SigmaProb &p, const T *__re
     }
 }
 
+// Alpha part of the 16 pairs [16 b, 16 b + 16) of determinant (ka, kb) for a
+// spin-flip-symmetric vector: each pair has at most one alpha excitation of
+// ka, read from the dense pair map as the offset of +-c[J][0] in the quantised
+// pair [c | -c] (C2), so an element is one predicated load and no arithmetic.
+// Every thread of a tile row reads the same map row (a broadcast).
+template <typename T>
+__device__ __forceinline__ void gather_alpha16(const SigmaProb &p, const T *__restrict__ C2, int ka, int kb, int b,
+                                               T (&x)[16]) {
+    if (16 * b >= p.np) {   // padding block of the last atom: the map row ends before it
+#pragma unroll
+        for (int k = 0; k < 16; k++) x[k] = T(0);
+        return;
+    }
+    const int4 *pm = reinterpret_cast<const int4 *>(p.pmap + ((size_t)ka * pmap_ld(p.np) + 16 * b));
+#pragma unroll
+    for (int g = 0; g < 4; g++) {
+        const int4 e4 = pm[g];
+        const int e[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+        for (int u = 0; u < 4; u++) x[4 * g + u] = e[u] >= 0 ? C2[(long long)e[u] + kb] : T(0);
+    }
+}
+
 }  // namespace tcg
 }  // namespace ifci

@@ -125,6 +125,77 @@ def test_fp64e_sigma_matches_fp64(handle, X):
     assert np.max(np.abs(a - b)) <= 5e-9 * np.max(np.abs(b))
 
 
+# ---------------------------------------------------------------- spin-flip-symmetric (alpha-only) gathers
+
+def _symmetric(c, nstr):
+    m = c.reshape(nstr, nstr)
+    return ((m + m.T) / 2).reshape(-1).contiguous()
+
+
+@pytest.mark.parametrize("prec,atol", [("fp64e", 1e-12), ("bf16", 1e-9)])
+@pytest.mark.parametrize("n,m", [(6, 2), (14, 2), (18, 2), (8, 4), (12, 4)])
+def test_symmetric_sigma_exact_on_dyadic_inputs(handle, prec, atol, n, m):
+    """Alpha-only gather + S + S^T on a symmetric dyadic vector equals the FP64
+    sigma of the full gather (tiles of several alpha rows at n = 6, one row
+    split in column tiles at n = 18 and 12)."""
+    h1, V = _dyadic_problem(n, seed=n * 10 + m + 2)
+    t = ifci.ifci_build_strings(handle, n, m)
+    rng = np.random.default_rng(n + 2)
+    c = torch.tensor(rng.integers(-3, 4, size=t.nstr * t.nstr) / 8.0, device=DEV)
+    c = _symmetric(c, t.nstr)          # multiples of 1/16: still exact
+    s64 = ifci.ifci_sigma(handle, t, h1, V, c, precision=ifci.IFCI_FP64)
+    ss = ifci.ifci_sigma(handle, t, h1, V, c, precision=ifci.PRECISIONS[prec], spin_symmetric=True)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(ss.cpu().numpy(), s64.cpu().numpy(), rtol=0, atol=atol)
+
+
+@pytest.mark.parametrize("X", [(0,), (0, 1), (5, 7), (8, 11, 12), "six"])
+def test_symmetric_fp64e_sigma_matches_oracle(handle, X):
+    """Same bound as the full-gather FP64E test, against the oracle's H c."""
+    chain = chain_24_uneven()
+    if X == "six":
+        X = tuple(b for b, s in enumerate(chain.body_sizes) if s == 6)[:3]
+    sysa = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=DEV),
+                             torch.tensor(chain.eri_packed(), device=DEV))
+    h1, eri, ecore = ifci.ifci_frozen_core(handle, sysa, X)
+    t = ifci.ifci_build_strings(handle, h1.shape[0], len(X))
+    c = _symmetric(torch.tensor(random_ci_vector(t.nstr, t.nstr, seed=13), device=DEV), t.nstr)
+    s64e = ifci.ifci_sigma(handle, t, h1, eri, c, precision=ifci.IFCI_FP64E, spin_symmetric=True)
+    torch.cuda.synchronize()
+    cn = c.cpu().numpy()
+    if t.nstr * t.nstr <= 40000:
+        H = fci.Hamiltonian(fci.subsystem(chain, X))
+        ref = H.matvec(cn) - ecore * cn
+    else:   # CAS(6e,18o): 64 seeded rows of the oracle
+        H = fci.Hamiltonian(fci.subsystem(chain, X))
+        rows = np.random.default_rng(3).choice(t.nstr * t.nstr, size=64, replace=False)
+        full = ifci.ifci_sigma(handle, t, h1, eri, c, precision=ifci.IFCI_FP64).cpu().numpy()
+        ref_rows = H.matvec_rows(cn, rows) - ecore * cn[rows]
+        np.testing.assert_allclose(full[rows], ref_rows, rtol=0, atol=1e-12 * np.max(np.abs(full)))
+        ref = full
+    a = s64e.cpu().numpy()
+    assert np.linalg.norm(a - ref) <= 5e-10 * np.linalg.norm(ref)
+    assert np.max(np.abs(a - ref)) <= 5e-9 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("X", [(0, 1), (8, 11, 12)])
+def test_symmetric_bf16_sigma_against_oracle(handle, X):
+    chain = chain_24_uneven()
+    sysa = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=DEV),
+                             torch.tensor(chain.eri_packed(), device=DEV))
+    h1, eri, ecore = ifci.ifci_frozen_core(handle, sysa, X)
+    t = ifci.ifci_build_strings(handle, h1.shape[0], len(X))
+    c = _symmetric(torch.tensor(random_ci_vector(t.nstr, t.nstr, seed=14), device=DEV), t.nstr)
+    sig = ifci.ifci_sigma(handle, t, h1, eri, c, precision=ifci.IFCI_BF16, spin_symmetric=True)
+    torch.cuda.synchronize()
+    H = fci.Hamiltonian(fci.subsystem(chain, X))
+    cn = c.cpu().numpy()
+    ref = H.matvec(cn) - ecore * cn
+    err = sig.cpu().numpy() - ref
+    assert np.linalg.norm(err) <= 4 * U_BF16 * np.linalg.norm(ref)
+    assert np.max(np.abs(err)) <= 16 * U_BF16 * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("prec,hi", [("fp64e", "fp64e"), ("bf16", "fp64e"), ("bf16", "fp64")])
 def test_tensor_core_davidson_reaches_fp64_accuracy(handle, prec, hi):
     chain = chain_24_uneven()
