@@ -136,18 +136,22 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
     for (int t = s_tile; t < ntile && ok;) {
         if (tid == 0) s_next = tcg::claim_tile(counter, probs, tiles, ntile);
         const WorkItem tile = tiles[t];
-        const SigmaProb &p = probs[tile.prob];
-        const int np = p.np, KA = k_atoms(np), n0 = tile.sub;
+        // descriptor fields in registers (the asm memory clobbers below would
+        // otherwise make the compiler reload them from global memory)
+        const SigmaProb &pg = probs[tile.prob];
+        const int np = pg.np, nstr = pg.nstr, sym = pg.sym;
+        const long long ndet = pg.ndet, doff = pg.doff;
+        const int32_t *pmap = pg.pmap;
+        const long long *C = Q + pg.qoff;   // round(c 2^38 / dscale) (and its negation when sym)
+        const int KA = k_atoms(np), n0 = tile.sub;
         const int Nt = round_up(min(kNT, np - n0), 16);
-        const long long ndet = p.ndet;
-        const int nstr = p.nstr;
         const tcg::TileGeom geo = tcg::tile_geom(tile.start, nstr);
         const bool live = row < geo.R * geo.Cw;
         const int r = live ? row / geo.Cw : 0;
         const int ka = geo.ka0 + r, kb = geo.kb0 + (live ? row % geo.Cw : 0);
         const long long K = (long long)ka * nstr + kb;
-        const long long *C = Q + p.qoff;   // round(c 2^38 / dscale)
-        uint32_t started = 0;      // accumulator levels already written in this tile
+        int4 pmn[4];               // pair-map row of this thread's next block
+        if (sym && live) tcg::pmap_load16(pmap, np, ka, q, pmn);
         for (int a = 0; a < KA; a++, g++) {
             // ---- loads of this atom's block (pairs 64a + 16q .. + 16): they overlap
             // the MMAs of the previous atom, which are still running
@@ -156,15 +160,23 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
 #pragma unroll
             for (int k = 0; k < 16; k++) x[k] = 0;
             if (live) {
-                if (p.sym) tcg::gather_alpha16<long long>(p, C, ka, kb, b, x);
-                else tcg::gather_block16<long long>(p, C, ka, kb, b, x);
+                if (sym) {
+                    int4 pmc[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) pmc[u] = pmn[u];
+                    if (a + 1 < KA) tcg::pmap_load16(pmap, np, ka, b + 4, pmn);
+                    tcg::gather_pm16<long long>(C, kb, pmc, x);
+                } else {
+                    tcg::gather_block16<long long>(probs[tile.prob], C, ka, kb, b, x);
+                }
             }
+            // MMAs of the previous atom done: A and W buffer (g + 1) & 1 are free
+            // (thread 0 polls, the others wait at the barrier)
             if (a > 0) {
-                if (!__syncthreads_and(mbar_wait(bm, ph_m))) { ok = false; break; }
+                if (!__syncthreads_and(tid == 0 ? (ok && mbar_wait(bm, ph_m)) : 1)) { ok = false; break; }
                 ph_m ^= 1;
             }
-            // the A buffer and W buffer (g + 1) & 1 are free now: prefetch the next stage
-            // (thread 0 wrote s_next itself, so it needs no barrier to read it)
+            // prefetch the next W stage (thread 0 wrote s_next itself: no barrier needed to read it)
             if (tid == 0) {
                 const int nt2 = a + 1 < KA ? t : s_next, na = a + 1 < KA ? a + 1 : 0;
                 if (nt2 < ntile)
@@ -194,41 +206,45 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            const uint32_t bwg = (g & 1) ? bw1 : bw0;
-            if (!__syncthreads_and(mbar_wait(bwg, (g >> 1) & 1))) { ok = false; break; }
+            __syncthreads();
+            // ---- one thread: wait for this stage's W, issue the 15 x (up to 4) MMAs
             if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t idesc = idesc_f16(kTM, Nt);
-                const uint32_t a0 = smem_u32(Asm), w0 = smem_u32(Wsm0 + (g & 1) * kWStage);
-                const int kst = min(4, (round_up(np, 16) - a * 64) / 16);
-                for (int j = 0; j < kS; j++) {
-                    for (int i = 0; i + j < kS; i++) {
-                        const int L = i + j;
-                        for (int ks = 0; ks < kst; ks++) {
-                            const uint32_t acc = (started >> L) & 1u;
-                            mma_f16(tmem + (uint32_t)(L * kNT),
-                                     smem_desc(a0 + (uint32_t)(j * kTM * kAtomBytes + ks * 32)),
-                                     smem_desc(w0 + (uint32_t)(i * kNT * kAtomBytes + ks * 32)), idesc, acc);
-                            started |= 1u << L;
-                        }
-                    }
+                ok = ok && mbar_wait((g & 1) ? bw1 : bw0, (g >> 1) & 1);
+                if (ok) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t idesc = idesc_f16(kTM, Nt);
+                    // descriptors of the stage bases; an offset below 256 KB adds (offset >> 4)
+                    const uint64_t ad0 = smem_desc(smem_u32(Asm));
+                    const uint64_t wd0 = smem_desc(smem_u32(Wsm0 + (g & 1) * kWStage));
+                    const int kst = min(4, (round_up(np, 16) - a * 64) / 16);
+#pragma unroll
+                    for (int j = 0; j < kS; j++)
+#pragma unroll
+                        for (int i = 0; i + j < kS; i++)
+#pragma unroll
+                            for (int ks = 0; ks < 4; ks++)
+                                if (ks < kst)
+                                    mma_f16(tmem + (uint32_t)((i + j) * kNT),
+                                            ad0 + (uint64_t)((j * kTM * kAtomBytes + ks * 32) >> 4),
+                                            wd0 + (uint64_t)((i * kNT * kAtomBytes + ks * 32) >> 4), idesc,
+                                            (a > 0 || j > 0 || ks > 0) ? 1u : 0u);
+                    mma_commit(bm);
                 }
-                mma_commit(bm);
             }
             __syncwarp();
         }
-        // the MMAs of the tile's last atom
-        if (ok) {
-            if (!__syncthreads_and(mbar_wait(bm, ph_m))) ok = false;
-            ph_m ^= 1;
-        }
+        // the MMAs of the tile's last atom (every thread reaches this barrier: a
+        // failed vote above made all of them leave the atom loop together, and
+        // thread 0 alone may hold ok = false from its W wait)
+        if (!__syncthreads_and(tid == 0 ? (ok && mbar_wait(bm, ph_m)) : ok)) ok = false;
+        ph_m ^= 1;
         if (!ok) break;
         // read before the closing barrier: thread 0 overwrites s_next after it
         const int t_next = s_next;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // ---- epilogue: the levels are exact integers below 2^24; combine them
         // in int64, G = sum_L acc_L 2^{8 (4 - L)}  (no FP64 arithmetic)
-        long long *Gp = G + p.doff;
+        long long *Gp = G + doff;
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         for (int c0 = 16 * (warp >> 2); c0 < Nt; c0 += 64) {
             long long gi[16];

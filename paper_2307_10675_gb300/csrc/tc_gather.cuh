@@ -139,23 +139,35 @@ __device__ __forceinline__ void gather_block16(const SigmaProb &p, const T *__re
 // spin-flip-symmetric vector: each pair has at most one alpha excitation of
 // ka, read from the dense pair map as the offset of +-c[J][0] in the quantised
 // pair [c | -c] (C2), so an element is one predicated load and no arithmetic.
-// Every thread of a tile row reads the same map row (a broadcast).
-template <typename T>
-__device__ __forceinline__ void gather_alpha16(const SigmaProb &p, const T *__restrict__ C2, int ka, int kb, int b,
-                                               T (&x)[16]) {
-    if (16 * b >= p.np) {   // padding block of the last atom: the map row ends before it
+// Every thread of a tile row reads the same map row (a broadcast).  Split in
+// two so that a kernel can fetch the map row of its next block early.
+__device__ __forceinline__ void pmap_load16(const int32_t *__restrict__ pmap, int np, int ka, int b, int4 (&pm)[4]) {
+    if (16 * b >= np) {   // padding block of the last atom: the map row ends before it
 #pragma unroll
-        for (int k = 0; k < 16; k++) x[k] = T(0);
+        for (int g = 0; g < 4; g++) pm[g] = make_int4(-1, -1, -1, -1);
         return;
     }
-    const int4 *pm = reinterpret_cast<const int4 *>(p.pmap + ((size_t)ka * pmap_ld(p.np) + 16 * b));
+    const int4 *src = reinterpret_cast<const int4 *>(pmap + ((size_t)ka * pmap_ld(np) + 16 * b));
+#pragma unroll
+    for (int g = 0; g < 4; g++) pm[g] = src[g];
+}
+
+template <typename T>
+__device__ __forceinline__ void gather_pm16(const T *__restrict__ C2, int kb, const int4 (&pm)[4], T (&x)[16]) {
 #pragma unroll
     for (int g = 0; g < 4; g++) {
-        const int4 e4 = pm[g];
-        const int e[4] = {e4.x, e4.y, e4.z, e4.w};
+        const int e[4] = {pm[g].x, pm[g].y, pm[g].z, pm[g].w};
 #pragma unroll
         for (int u = 0; u < 4; u++) x[4 * g + u] = e[u] >= 0 ? C2[(long long)e[u] + kb] : T(0);
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void gather_alpha16(const SigmaProb &p, const T *__restrict__ C2, int ka, int kb, int b,
+                                               T (&x)[16]) {
+    int4 pm[4];
+    pmap_load16(p.pmap, p.np, ka, b, pm);
+    gather_pm16<T>(C2, kb, pm, x);
 }
 
 }  // namespace tcg
