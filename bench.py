@@ -31,6 +31,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "iFCI increments/s & sigma TFLOP/s, 1 GB300, batched+mixed vs plain FP64 @1µEh"
+# dram__bytes_read.sum + dram__bytes_write.sum of one oz_contract_kernel launch
+# on CAS(6e,18o) (45.8 + 850.3 MB, 171 x 665,856 G elements); set to None
+# whenever that kernel changes until it is captured again
+OZ_DRAM_BYTES_PER_G_ELEMENT = (45.8e6 + 850.3e6) / (171 * 665856)
 UNIT = "increments/s"
 
 
@@ -48,9 +52,10 @@ def parse():
     ap.add_argument("--sample-seconds", type=float, default=20.0)
     ap.add_argument("--det-budget", type=int, default=0,
                     help="determinants per sigma wave (0: library default)")
-    ap.add_argument("--case", default="increments", choices=["increments", "sigma"],
+    ap.add_argument("--case", default="increments", choices=["increments", "sigma", "c2", "c4"],
                     help="sigma: time ifci_sigma alone on the workload's largest problem, CAS(6e,18o) "
-                         "(the small case for kernel profiles)")
+                         "(the small case for kernel profiles); c2: one CAS(14e,14o) CI per precision; "
+                         "c4: 3-body iFCI of the 40-body chain per precision, plus the RDM backward")
     return ap.parse_args()
 
 
@@ -212,6 +217,10 @@ def main():
 
     if args.case == "sigma":
         return sigma_case(args, torch, ifci)
+    if args.case == "c2":
+        return c2_case(args, torch, ifci)
+    if args.case == "c4":
+        return c4_case(args, torch, ifci)
 
     dist = None
     if world > 1:
@@ -273,10 +282,12 @@ def main():
     its = out["iters"]
     flops_step = 0.0
     exec_step = 0.0
+    gelems_step = 0.0
     for (X, n, k), it in zip(subs, its):
         nd, fl = cost_of(n, k)
         flops_step += it * fl
         exec_step += it * executed_oz_flops(n, k)
+        gelems_step += it * nd * (n * (n + 1) // 2)
     sig_ms = sum(prof[k][0] for k in ("gather", "contract", "contract_hi", "scatter")) / steps
     peaks = {}
     try:
@@ -297,8 +308,13 @@ def main():
         c_ms = prof["contract_hi"][0] / steps
         ach = flops_step / (c_ms / 1000.0) / 1e12
         pk = bf / 15.0
+        nlaunch = max(1, prof["contract_hi"][1] // steps)
         roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                "traffic": None, "kernel": "oz_contract_kernel",
+                "traffic": (OZ_DRAM_BYTES_PER_G_ELEMENT * gelems_step / nlaunch
+                            if OZ_DRAM_BYTES_PER_G_ELEMENT else None),
+                "traffic_note": "bytes per launch: dram read+write per G element of the ncu capture of "
+                                "oz_contract_kernel on CAS(6e,18o) x G elements per launch of this step",
+                "kernel": "oz_contract_kernel",
                 "peak_source": bf_src + " / 15 (15 BF16 slice products per FP64-accurate product)",
                 "executed_bf16_tflops": exec_step / (c_ms / 1000.0) / 1e12}
         dtype = "f64 (BF16 tensor-core emulation)"
@@ -400,6 +416,86 @@ def sigma_case(args, torch, ifci):
         line["contract_hi_tflops_algorithmic"] = fl / (c_ms / 1000.0) / 1e12
         line["contract_hi_executed_bf16_tflops"] = executed_oz_flops(n, m) / (c_ms / 1000.0) / 1e12
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def c2_case(args, torch, ifci):
+    """One large CI: CAS(14e,14o) of the seven-body chain (seed 2309), 11,778,624
+    determinants, lowest singlet, solved once per sigma precision (after one
+    untimed warm-up solve each); prints energies, their differences from the
+    FP64 path, iterations, wall time and sigma kernel time per precision."""
+    from synth import chain_7x2
+    dev = torch.device("cuda", 0)
+    chain = chain_7x2()
+    X = tuple(range(7))
+    runs = [("fp64", "fp64", "fp64"), ("fp32+fp64", "fp32", "fp64"), ("bf16+fp64", "bf16", "fp64"),
+            ("bf16+fp64e", "bf16", "fp64e"), ("fp64e", "fp64e", "fp64e")]
+    res = {}
+    with ifci.Handle(0, 0) as h:
+        sysd = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=dev),
+                                 torch.tensor(chain.eri_packed(), device=dev))
+        h1, eri, ecore = ifci.ifci_frozen_core(h, sysd, X)
+        for name, prec, hi in runs:
+            opts = ifci.davidson_opts(prec, hi_precision=hi, r_tol=1e-7, e_tol=1e-11, max_iter=200)
+            prob = ifci.CIProblem(14, 7, h1, eri, ecore)
+            ifci.ifci_davidson_batched(h, [prob], opts)
+            torch.cuda.synchronize(dev)
+            h.profile_enable(True)
+            t0 = time.perf_counter()
+            e, it, st = ifci.ifci_davidson_batched(h, [prob], opts)
+            torch.cuda.synchronize(dev)
+            wall = time.perf_counter() - t0
+            prof = h.profile_read()
+            h.profile_enable(False)
+            res[name] = {"energy": float(e[0]), "iters": int(it[0]), "status": int(st[0]), "seconds": wall,
+                         "sigma_ms": {k: v[0] for k, v in prof.items() if k != "vector" and v[0] > 0},
+                         "vector_ms": prof["vector"][0]}
+    e64 = res["fp64"]["energy"]
+    for name in res:
+        res[name]["minus_fp64_eh"] = res[name]["energy"] - e64
+    nd, fl = cost_of(14, 7)
+    print(json.dumps({"case": "c2", "workload": "CAS(14e,14o) of chain-7x2 (seed 2309), 11,778,624 determinants",
+                      "sigma_flops": fl, "davidson": {"r_tol": 1e-7, "e_tol": 1e-11}, "runs": res}), flush=True)
+    return 0
+
+
+def c4_case(args, torch, ifci):
+    """Production-scale 3-body iFCI of the 40-body uneven chain (seed 2310):
+    10,700 body sets up to CAS(6e,18o), one timed ifci_increments per
+    precision (FP64E, mixed BF16 + FP64E, plain FP64; no warm-up: each run
+    builds its own tables and plans), then the RDM backward of the FP64E run.
+    Prints E_total per path, its difference from the plain FP64 path and
+    increments/s."""
+    from synth import chain_40_uneven
+    dev = torch.device("cuda", 0)
+    chain = chain_40_uneven()
+    sysd = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=dev),
+                             torch.tensor(chain.eri_packed(), device=dev))
+    nsub = len(subset_sizes(chain, 3))
+    paths = [("fp64e", "fp64e", "fp64e"), ("bf16+fp64e", "bf16", "fp64e"), ("fp64", "fp64", "fp64")]
+    res = {}
+    with ifci.Handle(0, 0) as h:
+        for name, prec, hi in paths:
+            opts = ifci.davidson_opts(prec, hi_precision=hi, r_tol=1e-6, e_tol=1e-10, max_iter=300)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            out = ifci.ifci_increments(h, sysd, 3, opts)
+            torch.cuda.synchronize(dev)
+            wall = time.perf_counter() - t0
+            res[name] = {"e_total": out["e_total"], "seconds": wall, "increments_per_s": nsub / wall,
+                         "unconverged": int(np.sum(out["status"] != 0)), "iters_mean": float(np.mean(out["iters"]))}
+            if name == "fp64e":
+                t0 = time.perf_counter()
+                dh, dV = ifci.ifci_rdm_backward(h, sysd, 3, 1.0, opts)
+                torch.cuda.synchronize(dev)
+                res[name]["rdm_backward_seconds"] = time.perf_counter() - t0
+                res[name]["euler_identity_minus_e_total"] = float(
+                    (torch.sum(sysd.h * dh) + torch.sum(sysd.eri * dV)).item() - out["e_total"])
+                del dh, dV
+    for name in res:
+        res[name]["minus_fp64_eh"] = res[name]["e_total"] - res["fp64"]["e_total"]
+    print(json.dumps({"case": "c4", "workload": "chain-40-uneven (seed 2310), iFCI to 3 bodies, "
+                      f"{nsub} CI problems, max CAS(6e,18o)", "runs": res}), flush=True)
     return 0
 
 

@@ -53,7 +53,7 @@ static void dav_layout(const std::vector<ProbSpec> &specs, const ifci_davidson_o
     z.bytes += 2 * ws_round((size_t)budget * eb);                          // D, G
     z.bytes += ws_round(n * sizeof(DavProb)) + ws_round(n * sizeof(DavState)) + ws_round(z.nitem * sizeof(WorkItem));
     z.bytes += ws_round((size_t)z.nitem * kNP * 8) + ws_round(n * kMaxSpace * kMaxSpace * 8) +
-               2 * ws_round(n * kNP * 8) + ws_round(8) + 2 * ws_round(n * 4);
+               ws_round(n * kYStride * 8) + ws_round(n * kNP * 8) + ws_round(8) + 2 * ws_round(n * 4);
     z.bytes += ws_round(n * sizeof(FoldDesc)) + ws_round(n * sizeof(HdiagDesc));
     z.bytes += ws_round((size_t)z.nitem * sizeof(int)) + ws_round((size_t)z.nitem * sizeof(long long));
     // two sigma plans (hi and lo)
@@ -135,6 +135,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
     DavBatch b;
     b.nprob = n;
     b.max_space = ms;
+    b.keep = std::min(kKeep, ms - 2);
     b.precision = o.precision;
     b.hi_precision = hi_prec;
     b.max_iter = o.max_iter;
@@ -197,7 +198,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
     b.d_vitems = ws_take<WorkItem>(h, b.vitems.size());
     b.d_part = ws_take<double>(h, b.vitems.size() * kNP);
     b.d_gs = ws_take<double>(h, (size_t)n * kMaxSpace * kMaxSpace);
-    b.d_y = ws_take<double>(h, (size_t)n * kNP);
+    b.d_y = ws_take<double>(h, (size_t)n * kYStride);
     b.d_coef = ws_take<double>(h, (size_t)n * kNP);
     b.d_nactive = ws_take<int>(h, 2);
     int *d_hi = ws_take<int>(h, n), *d_lo = ws_take<int>(h, n);
@@ -236,7 +237,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
     IFCI_CUDA_TRY(h, cudaMemcpyAsync(b.d_vitems, b.vitems.data(), b.vitems.size() * sizeof(WorkItem),
                                      cudaMemcpyHostToDevice, s));
     IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_gs, 0, (size_t)n * kMaxSpace * kMaxSpace * 8, s));
-    IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_y, 0, (size_t)n * kNP * 8, s));
+    IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_y, 0, (size_t)n * kYStride * 8, s));
     int maxnp = 0;
     for (const ProbSpec &p : specs) maxnp = std::max(maxnp, p.n * (p.n + 1) / 2);
     IFCI_TRY(launch_fold(h, n, d_fold, maxnp, s));

@@ -10,11 +10,19 @@
 //   -> residual r = sum_j y_j (sigma_j - theta b_j), correction t = r / (theta - H_II)
 //   -> classical Gram-Schmidt twice -> normalise, symmetrise (c = c^T sector).
 //
+// A full subspace restarts thick: it keeps the lowest Ritz vectors (up to
+// kKeep, with their sigmas and a diagonal projected matrix) plus the new
+// correction, so a near-degenerate pair of lowest states stays resolved by
+// Rayleigh-Ritz instead of being found again after each restart.
+//
 // Two precisions of sigma (mixed mode): corrections get the low-precision
 // sigma; each restart vector x (the current Ritz vector) gets the FP64 sigma,
 // and convergence is only judged on x, whose Rayleigh quotient and residual
 // are then exact to FP64 rounding.  The low-precision error enters only
-// through the corrections, whose weight shrinks with the residual.
+// through the corrections, whose weight shrinks with the residual.  A
+// problem whose exact residual does not halve over a restart cycle (the low
+// precision cannot resolve its spectrum, e.g. a gap below the rounding of the
+// projected matrix) switches to the FP64-accurate sigma for every vector.
 #include <algorithm>
 #include <cmath>
 
@@ -168,8 +176,8 @@ __global__ void select_kernel(const DavState *__restrict__ st, int nprob, int mi
     const DavState s = st[i];
     int a = s.active;
     if (mixed) {
-        hi[i] = a && s.k == 1;
-        lo[i] = a && s.k > 1;
+        hi[i] = a && (s.k == 1 || s.exact_all);
+        lo[i] = a && s.k > 1 && !s.exact_all;
     } else {
         hi[i] = a;
         lo[i] = 0;
@@ -192,7 +200,7 @@ __global__ void __launch_bounds__(256) dots_kernel(const DavProb *__restrict__ p
     if (!s.active) return;
     const DavProb &p = probs[it.prob];
     const int k = s.newest + 1;
-    const bool exact0 = mixed && s.newest > 0;
+    const bool exact0 = mixed && !s.exact_all && s.newest > 0;
     double acc[kMaxSpace + 1];
 #pragma unroll
     for (int j = 0; j <= kMaxSpace; j++) acc[j] = 0.0;
@@ -210,8 +218,9 @@ __global__ void __launch_bounds__(256) dots_kernel(const DavProb *__restrict__ p
     block_sum_store<kMaxSpace + 1>(acc, k, part + (long long)blockIdx.x * kNP);
 }
 
-// Cyclic Jacobi on a symmetric k x k matrix (k <= kMaxSpace): lowest eigenpair.
-__device__ void jacobi_lowest(double *A, double *V, int k, double *theta, double *y) {
+// Cyclic Jacobi on a symmetric k x k matrix (k <= kMaxSpace): the nk <= k
+// lowest eigenpairs, theta[r] and y[r * kMaxSpace + i].
+__device__ void jacobi_lowest(double *A, double *V, int k, int nk, double *theta, double *y) {
     for (int i = 0; i < k; i++)
         for (int j = 0; j < k; j++) V[i * kMaxSpace + j] = (i == j) ? 1.0 : 0.0;
     for (int sweep = 0; sweep < 60; sweep++) {
@@ -248,16 +257,22 @@ __device__ void jacobi_lowest(double *A, double *V, int k, double *theta, double
                 }
             }
     }
-    int best = 0;
-    for (int i = 1; i < k; i++)
-        if (A[i * kMaxSpace + i] < A[best * kMaxSpace + best]) best = i;
-    *theta = A[best * kMaxSpace + best];
-    // fix the sign so that the largest component is positive (deterministic)
-    int big = 0;
-    for (int i = 1; i < k; i++)
-        if (fabs(V[i * kMaxSpace + best]) > fabs(V[big * kMaxSpace + best])) big = i;
-    double sg = V[big * kMaxSpace + best] < 0 ? -1.0 : 1.0;
-    for (int i = 0; i < k; i++) y[i] = sg * V[i * kMaxSpace + best];
+    // the nk lowest eigenpairs in ascending order; each vector's largest
+    // component made positive (deterministic sign)
+    bool used[kMaxSpace];
+    for (int i = 0; i < k; i++) used[i] = false;
+    for (int r = 0; r < nk; r++) {
+        int best = -1;
+        for (int i = 0; i < k; i++)
+            if (!used[i] && (best < 0 || A[i * kMaxSpace + i] < A[best * kMaxSpace + best])) best = i;
+        used[best] = true;
+        theta[r] = A[best * kMaxSpace + best];
+        int big = 0;
+        for (int i = 1; i < k; i++)
+            if (fabs(V[i * kMaxSpace + best]) > fabs(V[big * kMaxSpace + best])) big = i;
+        double sg = V[big * kMaxSpace + best] < 0 ? -1.0 : 1.0;
+        for (int i = 0; i < k; i++) y[r * kMaxSpace + i] = sg * V[i * kMaxSpace + best];
+    }
 }
 
 // One block per problem: finish the subspace column and solve the projected problem.
@@ -281,13 +296,17 @@ __global__ void solve_kernel(const DavProb *__restrict__ probs, DavState *__rest
             Gm[j * kMaxSpace + s.newest] = col[j];
             Gm[s.newest * kMaxSpace + j] = col[j];
         }
-        double A[kMaxSpace * kMaxSpace], V[kMaxSpace * kMaxSpace], y[kMaxSpace];
+        double A[kMaxSpace * kMaxSpace], V[kMaxSpace * kMaxSpace], y[kKeep * kMaxSpace], th[kKeep];
         for (int a = 0; a < k; a++)
             for (int b = 0; b < k; b++) A[a * kMaxSpace + b] = 0.5 * (Gm[a * kMaxSpace + b] + Gm[b * kMaxSpace + a]);
-        double theta;
-        jacobi_lowest(A, V, k, &theta, y);
-        for (int j = 0; j < kNP; j++) ys[(long long)i * kNP + j] = j < k ? y[j] : 0.0;
-        s.theta = theta;
+        const int nk = k < kKeep ? k : kKeep;
+        jacobi_lowest(A, V, k, nk, th, y);
+        double *yo = ys + (long long)i * kYStride;
+        for (int r = 0; r < kKeep; r++) {
+            for (int j = 0; j < kNP; j++) yo[r * kNP + j] = (r < nk && j < k) ? y[r * kMaxSpace + j] : 0.0;
+            yo[r * kNP + kMaxSpace] = r < nk ? th[r] : 0.0;
+        }
+        s.theta = th[0];
         s.iters += 1;
         st[i] = s;
     }
@@ -307,7 +326,7 @@ __global__ void __launch_bounds__(256) residual_kernel(const DavProb *__restrict
     const double theta = s.theta;
     double y[kMaxSpace];
 #pragma unroll
-    for (int j = 0; j < kMaxSpace; j++) y[j] = ys[(long long)it.prob * kNP + j];
+    for (int j = 0; j < kMaxSpace; j++) y[j] = ys[(long long)it.prob * kYStride + j];
     double acc[kMaxSpace + 2];
 #pragma unroll
     for (int j = 0; j < kMaxSpace + 2; j++) acc[j] = 0.0;
@@ -354,8 +373,8 @@ __global__ void __launch_bounds__(256) residual_kernel(const DavProb *__restrict
 // Convergence test, restart decision, CGS coefficients.  One block per problem.
 __global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st,
                              const double *__restrict__ part, double *__restrict__ coef, const double *__restrict__ ys,
-                             double *__restrict__ gs, int max_space, int restart_at, int mixed, int max_iter,
-                             double e_tol, double r_tol, int *__restrict__ nactive) {
+                             double *__restrict__ gs, int max_space, int restart_at, int keep_max, int mixed,
+                             int max_iter, double e_tol, double r_tol, int *__restrict__ nactive) {
     const int i = blockIdx.x;
     DavState s = st[i];
     if (!s.active) return;
@@ -370,12 +389,19 @@ __global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__rest
     __syncthreads();
     if (threadIdx.x != 0) return;
     s.rnorm = sqrt(sum[kMaxSpace + 1]);
-    const double *y = ys + (long long)i * kNP;
-    bool exact = !mixed || k == 1;
+    const double *ys_i = ys + (long long)i * kYStride;
+    const bool lowmix = mixed && !s.exact_all;   // this problem still uses the low-precision sigma
+    bool exact = !lowmix || k == 1;
     // mixed mode judges only FP64-exact residuals, so the residual alone decides
     // (energy error ~ r^2 / gap); the FP64 path also asks for a settled energy
-    bool conv = exact && s.rnorm < r_tol && (mixed || fabs(s.theta - s.theta_prev) < e_tol);
+    bool conv = exact && s.rnorm < r_tol && (lowmix || fabs(s.theta - s.theta_prev) < e_tol);
     if (exact) s.theta_prev = s.theta;
+    if (lowmix && k == 1 && !conv) {
+        // a restart cycle of low-precision corrections must at least halve the
+        // exact residual; otherwise take the exact sigma for every vector from now on
+        if (s.rnorm_exact_prev > 0.0 && s.rnorm > 0.5 * s.rnorm_exact_prev) s.exact_all = 1;
+        s.rnorm_exact_prev = s.rnorm;
+    }
     if (conv || s.rnorm == 0.0) {
         s.active = 0;
         s.status = IFCI_OK;
@@ -398,24 +424,31 @@ __global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__rest
     // the spin-flip-even sector has nstr (nstr + 1) / 2 dimensions: a full
     // subspace restarts (mixed mode) so that its final check is FP64-exact
     const int nsym = p.nstr * (p.nstr + 1) / 2;
-    if (k >= restart_at || (mixed && (k >= nsym || s.force))) {
+    const int ra = lowmix ? restart_at : max_space;
+    if (k >= ra || (lowmix && (k >= nsym || s.force))) {
         s.force = 0;
         s.restart = 1;
         s.kold = k;
-        if (mixed) {
+        if (lowmix) {
             // basis becomes [x]; its FP64 sigma is built next iteration
             s.k = 1;
             s.newest = 0;
             s.tslot = -1;
         } else {
-            // basis becomes [x, t]; <x|t> = sum_j y_j <b_j|t>
-            double xt = 0.0;
-            for (int j = 0; j < k; j++) xt += y[j] * sum[j];
-            c[0] = xt;
-            for (int j = 1; j < kNP; j++) c[j] = 0.0;
-            s.k = 1;
-            s.tslot = 1;
-            Gm[0] = s.theta;
+            // thick restart: basis becomes [x_0 .. x_{keep-1}, t] with the lowest
+            // Ritz vectors x_r = sum_j Y_r[j] b_j (projected matrix diag(theta_r))
+            // and <x_r|t> = sum_j Y_r[j] <b_j|t>
+            const int keep = min(keep_max, k);
+            for (int j = 0; j < kNP; j++) c[j] = 0.0;
+            for (int r = 0; r < keep; r++) {
+                double xt = 0.0;
+                for (int j = 0; j < k; j++) xt += ys_i[r * kNP + j] * sum[j];
+                c[r] = xt;
+            }
+            for (int a = 0; a < keep; a++)
+                for (int b2 = 0; b2 < keep; b2++) Gm[a * kMaxSpace + b2] = a == b2 ? ys_i[a * kNP + kMaxSpace] : 0.0;
+            s.k = keep;
+            s.tslot = keep;
         }
     } else {
         s.restart = 0;
@@ -426,7 +459,11 @@ __global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__rest
     st[i] = s;
 }
 
-// Restart: B_0 <- sum y_j B_j, S_0 <- sum y_j S_j, slot 1 <- correction (FP64 mode).
+// Restart.  Low-precision mixed mode: B_0 <- x = sum_j y_j B_j (its sigma is
+// rebuilt exactly next).  Otherwise (thick): B_r <- sum_j Y_r[j] B_j and
+// S_r <- sum_j Y_r[j] S_j for the kept Ritz vectors r < keep, and the
+// correction moves from the scratch slot to slot keep.  Every old slot of an
+// element is read before any is written.
 __global__ void __launch_bounds__(256) restart_kernel(const DavProb *__restrict__ probs,
                                                       const DavState *__restrict__ st,
                                                       const WorkItem *__restrict__ items, const double *__restrict__ ys,
@@ -435,24 +472,33 @@ __global__ void __launch_bounds__(256) restart_kernel(const DavProb *__restrict_
     const DavState s = st[it.prob];
     if (!s.active || !s.restart) return;
     const DavProb &p = probs[it.prob];
-    double y[kMaxSpace];
-#pragma unroll
-    for (int j = 0; j < kMaxSpace; j++) y[j] = ys[(long long)it.prob * kNP + j];
+    const bool thick = !mixed || s.exact_all;
+    const int keep = thick ? s.k : 1;
+    const double *yr = ys + (long long)it.prob * kYStride;
     long long end = min(it.start + (long long)kVecChunk, p.ndet);
     const double *T = p.B + (long long)max_space * p.ndet;
     const int kk = s.kold;   // only the slots of the old subspace are read
     for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) {
-        double x = 0.0, sx = 0.0;
+        double bv[kMaxSpace], sv[kMaxSpace];
 #pragma unroll
         for (int j = 0; j < kMaxSpace; j++) {
-            if (j < kk) {
-                x += y[j] * p.B[(long long)j * p.ndet + I];
-                sx += y[j] * p.S[(long long)j * p.ndet + I];
+            bv[j] = j < kk ? p.B[(long long)j * p.ndet + I] : 0.0;
+            sv[j] = j < kk ? p.S[(long long)j * p.ndet + I] : 0.0;
+        }
+#pragma unroll
+        for (int r = 0; r < kKeep; r++) {
+            if (r < keep) {
+                double x = 0.0, sx = 0.0;
+#pragma unroll
+                for (int j = 0; j < kMaxSpace; j++) {
+                    x += yr[r * kNP + j] * bv[j];
+                    sx += yr[r * kNP + j] * sv[j];
+                }
+                p.B[(long long)r * p.ndet + I] = x;
+                p.S[(long long)r * p.ndet + I] = sx;
             }
         }
-        p.B[I] = x;
-        p.S[I] = sx;
-        if (!mixed) p.B[p.ndet + I] = T[I];
+        if (thick) p.B[(long long)keep * p.ndet + I] = T[I];
     }
 }
 
@@ -469,7 +515,7 @@ __global__ void __launch_bounds__(256) ortho_kernel(const DavProb *__restrict__ 
     double c[kMaxSpace];
 #pragma unroll
     for (int j = 0; j < kMaxSpace; j++) c[j] = coef[(long long)it.prob * kNP + j];
-    double *T = p.B + (long long)(s.restart ? 1 : s.tslot) * p.ndet;
+    double *T = p.B + (long long)s.tslot * p.ndet;
     if (!s.restart && s.tslot == k) T = p.B + (long long)max_space * p.ndet;
     double acc[kMaxSpace + 1];
 #pragma unroll
@@ -533,7 +579,7 @@ __global__ void __launch_bounds__(256) normalize_kernel(const DavProb *__restric
     if (!s.active || s.tslot < 0) return;
     const DavProb &p = probs[it.prob];
     const double inv = s.tnorm2 > 0.0 ? 1.0 / sqrt(s.tnorm2) : 0.0;
-    double *T = p.B + (long long)(s.restart ? 1 : s.tslot) * p.ndet;
+    double *T = p.B + (long long)s.tslot * p.ndet;
     double *dst = T;
     if (!s.restart && s.tslot == s.k) {
         T = p.B + (long long)max_space * p.ndet;
@@ -557,7 +603,7 @@ __global__ void advance_kernel(const DavProb *__restrict__ probs, DavState *__re
     if (i >= nprob) return;
     DavState s = st[i];
     if (!s.active) return;
-    if (s.tslot >= 0 && s.tnorm2 < 1e-28 && mixed) {
+    if (s.tslot >= 0 && s.tnorm2 < 1e-28 && mixed && !s.exact_all) {
         // mixed mode: keep the subspace, rebuild sigma of the newest vector and
         // restart at the next check, whose sigma of x is FP64-exact
         s.force = 1;
@@ -574,9 +620,8 @@ __global__ void advance_kernel(const DavProb *__restrict__ probs, DavState *__re
         return;
     }
     if (s.tslot >= 0) {
-        int slot = s.restart ? 1 : s.tslot;
-        s.newest = slot;
-        s.k = slot + 1;
+        s.newest = s.tslot;
+        s.k = s.tslot + 1;
     }
     s.restart = 0;
     st[i] = s;
@@ -594,7 +639,7 @@ __global__ void __launch_bounds__(256) ritz_out_kernel(const DavProb *__restrict
     const int k = s.newest + 1;
     double y[kMaxSpace];
 #pragma unroll
-    for (int j = 0; j < kMaxSpace; j++) y[j] = ys[(long long)it.prob * kNP + j];
+    for (int j = 0; j < kMaxSpace; j++) y[j] = ys[(long long)it.prob * kYStride + j];
     long long end = min(it.start + (long long)kVecChunk, p.ndet);
     for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) {
         double x = 0.0;
@@ -635,10 +680,10 @@ int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_
         residual_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, b.d_part);
         IFCI_LAUNCH_CHECK(h);
         IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_nactive, 0, sizeof(int), s));
-        // the restart kernel needs the subspace size before check_kernel shrinks it:
-        // it is always restart_at when a restart happens
+        // check_kernel records the subspace size before a restart (kold) for restart_kernel
         check_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_coef, b.d_y, b.d_gs, b.max_space,
-                                            restart_at, mixed ? 1 : 0, b.max_iter, b.e_tol, b.r_tol, b.d_nactive);
+                                            restart_at, b.keep, mixed ? 1 : 0, b.max_iter, b.e_tol, b.r_tol,
+                                            b.d_nactive);
         IFCI_LAUNCH_CHECK(h);
         restart_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, mixed ? 1 : 0);
         IFCI_LAUNCH_CHECK(h);

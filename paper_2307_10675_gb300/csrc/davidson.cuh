@@ -27,15 +27,25 @@ struct DavState {
     long long ref;           // index of the lowest-diagonal determinant (start vector)
     int force;               // mixed mode: restart at the next check (subspace exhausted)
     int kold;                // subspace size just before the last restart
+    int exact_all;           // mixed mode: this problem now takes the exact sigma for every vector
+    int pad_;
     double theta, theta_prev, rnorm, tnorm2, energy;
+    double rnorm_exact_prev; // mixed mode: residual norm at the previous exact check
 };
 
 constexpr int kVecChunk = 4096;   // determinants per vector work item
 constexpr int kMaxSpace = 24;
 constexpr int kNP = kMaxSpace + 2;
+// thick restart keeps the lowest kKeep Ritz vectors (a near-degenerate pair
+// of lowest states is resolved by Rayleigh-Ritz instead of being re-found
+// after every restart); ys holds kKeep Ritz vectors per problem, kNP doubles
+// each, the Ritz value of vector r at [r * kNP + kMaxSpace]
+constexpr int kKeep = 3;
+constexpr int kYStride = kKeep * kNP;
 
 struct DavBatch {
     int nprob = 0, max_space = 12;
+    int keep = kKeep;             // Ritz vectors kept at a thick restart (<= max_space - 2)
     int precision = IFCI_FP64;
     int hi_precision = IFCI_FP64;
     int max_iter = 100;
@@ -47,7 +57,7 @@ struct DavBatch {
     WorkItem *d_vitems = nullptr;
     double *d_part = nullptr;     // [nitem][kNP]
     double *d_gs = nullptr;       // [nprob][kMaxSpace*kMaxSpace]
-    double *d_y = nullptr;        // [nprob][kNP]
+    double *d_y = nullptr;        // [nprob][kYStride] lowest Ritz vectors and values
     double *d_coef = nullptr;     // [nprob][kNP]
     int *d_nactive = nullptr;
 };
