@@ -165,6 +165,19 @@ size_t ifci_sigma_noalloc_max_bytes(void);
 int ifci_sigma_noalloc(const ifci_strings_t *str, const double *h1, const double *eri,
                        const double *c, double *sigma, ifci_stream_t stream);
 
+/* ifci_h_elements — single matrix elements <I|H|J> of the same H (no
+ * constant) between determinants, by the Slater–Condon rules on the string
+ * bit masks (the Davidson solver uses them for its start vectors: the lowest
+ * eigenvector of H among the lowest-diagonal determinants).  The paper has no
+ * separate call for this; it is exposed so that the rules can be checked
+ * element by element.
+ *   bra, ket : device int64[count], determinant indices I = I_a * nstr + I_b.
+ *   out      : device double[count].
+ * Asynchronous on `stream`; INVALID_ARG for an inconsistent string table. */
+int ifci_h_elements(ifci_handle_t handle, const ifci_strings_t *str, const double *h1, const double *eri,
+                    long long count, const long long *bra, const long long *ket, double *out,
+                    ifci_stream_t stream);
+
 /* ifci_hdiag — diagonal <I|H|I> of the same H (no constant), for the
  * Davidson preconditioner.  hd: device double[nstr*nstr].  Asynchronous. */
 int ifci_hdiag(ifci_handle_t handle, const ifci_strings_t *str,

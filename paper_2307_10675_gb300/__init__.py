@@ -7,7 +7,7 @@ from .api import (  # noqa: F401
     IFCI_BF16, IFCI_FP32, IFCI_FP64, IFCI_FP64E, IFCI_TF32, PRECISIONS,
     CIProblem, Handle, IfciEnergy, IfciError, StringTables, SystemArrays, ifci_energy,
     body_subsets, davidson_opts,
-    ifci_build_strings, ifci_davidson_batched, ifci_frozen_core, ifci_hdiag, ifci_increments,
+    ifci_build_strings, ifci_davidson_batched, ifci_frozen_core, ifci_h_elements, ifci_hdiag, ifci_increments,
     ifci_num_subsets, ifci_rdm_backward, ifci_sigma, ifci_sigma_noalloc, ifci_sigma_noalloc_max_bytes,
     ifci_string_counts,
 )

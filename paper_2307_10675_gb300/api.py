@@ -163,6 +163,17 @@ def ifci_sigma_noalloc_max_bytes() -> int:
     return int(_lib().ifci_sigma_noalloc_max_bytes())
 
 
+def ifci_h_elements(handle: Handle, tables: StringTables, h1: torch.Tensor, eri: torch.Tensor,
+                    bra: torch.Tensor, ket: torch.Tensor, stream=None) -> torch.Tensor:
+    """<I|H|J> for int64 determinant index pairs (device tensors)."""
+    bra = bra.to(torch.int64).contiguous()
+    ket = ket.to(torch.int64).contiguous()
+    out = torch.empty(bra.numel(), dtype=torch.float64, device=bra.device)
+    handle.check(_lib().ifci_h_elements(handle.ptr, tables.as_c(), _ptr(h1), _ptr(eri), int(bra.numel()),
+                                        _ptr(bra), _ptr(ket), _ptr(out), _stream(stream)))
+    return out
+
+
 def ifci_hdiag(handle: Handle, tables: StringTables, h1: torch.Tensor, eri: torch.Tensor,
                hd: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     if hd is None:

@@ -54,7 +54,7 @@ static void dav_layout(const std::vector<ProbSpec> &specs, const ifci_davidson_o
     z.bytes += ws_round(n * sizeof(DavProb)) + ws_round(n * sizeof(DavState)) + ws_round(z.nitem * sizeof(WorkItem));
     z.bytes += ws_round((size_t)z.nitem * kNP * 8) + ws_round(n * kMaxSpace * kMaxSpace * 8) +
                ws_round(n * kYStride * 8) + ws_round(n * kNP * 8) + ws_round(8) + 2 * ws_round(n * 4);
-    z.bytes += ws_round(n * sizeof(FoldDesc)) + ws_round(n * sizeof(HdiagDesc));
+    z.bytes += ws_round(n * sizeof(FoldDesc)) + ws_round(n * sizeof(HdiagDesc)) + psp_workspace_bytes((int)n);
     z.bytes += ws_round((size_t)z.nitem * sizeof(int)) + ws_round((size_t)z.nitem * sizeof(long long));
     // two sigma plans (hi and lo)
     z.bytes += 2 * (ws_round(n * sizeof(SigmaProb)) + ws_round((size_t)z.n_items_sigma * sizeof(WorkItem)) +
@@ -245,7 +245,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
     if (tc) IFCI_TRY(launch_tc_pack_w(h, n, lop.d_probs, o.precision, s));
     if (oz) IFCI_TRY(launch_oz_pack_w(h, n, hi.d_probs, s));
     IFCI_TRY(launch_hdiag(h, d_hd, d_hwp, d_hws, (int)hw_prob.size(), kVecChunk, s));
-    IFCI_TRY(dav_init(h, b, s));
+    IFCI_TRY(dav_init(h, b, d_hd, s));
 
     int *h_nactive = nullptr;
     IFCI_CUDA_TRY(h, cudaMallocHost(&h_nactive, 2 * sizeof(int)));

@@ -1,6 +1,7 @@
 // Host-side Davidson driver shared by ifci_davidson_batched and ifci_increments.
 #pragma once
 #include "davidson.cuh"
+#include "hamiltonian.cuh"
 
 namespace ifci {
 
@@ -28,7 +29,9 @@ size_t dav_workspace_bytes(const std::vector<ProbSpec> &specs, const ifci_davids
 // except energies).  Synchronous.
 int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o, double *energies,
               int *iters, int *status, cudaStream_t s);
-int dav_init(ifci_handle_t h, DavBatch &b, cudaStream_t s);
+int dav_init(ifci_handle_t h, DavBatch &b, const HdiagDesc *d_hd, cudaStream_t s);
+size_t psp_workspace_bytes(int nprob);
+int launch_pspace_start(ifci_handle_t h, const DavBatch &b, const HdiagDesc *d_hd, cudaStream_t s);
 int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_plan, int *d_hi, int *d_lo,
                 void *D, void *G, int *h_nactive, cudaStream_t s);
 

@@ -15,14 +15,16 @@
 // correction, so a near-degenerate pair of lowest states stays resolved by
 // Rayleigh-Ritz instead of being found again after each restart.
 //
-// Two precisions of sigma (mixed mode): corrections get the low-precision
-// sigma; each restart vector x (the current Ritz vector) gets the FP64 sigma,
-// and convergence is only judged on x, whose Rayleigh quotient and residual
-// are then exact to FP64 rounding.  The low-precision error enters only
-// through the corrections, whose weight shrinks with the residual.  A
-// problem whose exact residual does not halve over a restart cycle (the low
-// precision cannot resolve its spectrum, e.g. a gap below the rounding of the
-// projected matrix) switches to the FP64-accurate sigma for every vector.
+// Two precisions of sigma (mixed mode), in two phases per problem.  Phase 1
+// builds every sigma in the low precision (thick restarts as above) and never
+// declares convergence: its residual is only as good as the low-precision
+// sigma.  When that residual stops halving between restarts, falls below
+// 10 r_tol, or half of max_iter is spent, the problem keeps its lowest Ritz
+// vectors, rebuilds their exact (FP64 or FP64-accurate) sigmas one per
+// iteration, and continues as the exact solver, whose Rayleigh quotients and
+// residuals decide convergence.  The low-precision Rayleigh-Ritz may misorder
+// states closer than its rounding, but it keeps them among the lowest Ritz
+// vectors, and the first exact Rayleigh-Ritz over those picks the lowest.
 #include <algorithm>
 #include <cmath>
 
@@ -60,16 +62,14 @@ __device__ void block_sum_store(double (&v)[NV], int nv, double *out) {
 
 // ------------------------------------------------------------------ setup
 
-// Starting vector: the determinant of lowest diagonal H_II (with its mirror
-// image (I_b, I_a), to stay in the spin-flip-even sector) plus a small
-// deterministic pseudo-random symmetric component.  The random part gives the
-// start vector a nonzero overlap with every state of the sector: a single
-// determinant can be orthogonal to the lowest singlet (a charge-transfer
-// ground state), and the Davidson iteration would then converge to an
-// excited state.
-constexpr double kStartNoise = 0.1;   // norm of the random part before normalisation
+// Start block (orthonormal, its sigmas built one per iteration before the
+// first correction): the lowest eigenvectors of H in the pair functions of the
+// lowest-diagonal determinants (pspace.cu), which can lie in different
+// symmetry classes of H, and a deterministic pseudo-random symmetric vector
+// that gives the subspace a nonzero overlap with every state of the
+// spin-flip-even sector.
 
-__global__ void init_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st) {
+__global__ void init_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st, int max_space) {
     const DavProb p = probs[blockIdx.x];
     __shared__ double bv[256];
     __shared__ long long bi[256];
@@ -109,6 +109,12 @@ __global__ void init_kernel(const DavProb *__restrict__ probs, DavState *__restr
         s.rnorm = 1e300;
         s.tnorm2 = 0.0;
         s.energy = 0.0;
+        int nv, ns;
+        start_block(p.nstr, max_space, &nv, &ns);
+        s.noise_slot = ns;
+        s.tgt = 0;
+        for (int r = 0; r < kKeep; r++) s.rn[r] = 1e300;
+        s.rebuild_to = nv + (ns >= 0 ? 1 : 0);   // sigmas of the start block, one per iteration
         st[blockIdx.x] = s;
     }
 }
@@ -123,52 +129,45 @@ __device__ __forceinline__ double pair_noise(int a, int b) {
     return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
-// B_0 = e_ref (+ mirror) + kStartNoise * r / |r|_est ; partial |B_0|^2 per item
+// Start block: the P-space slots 0..nv-1 zeroed (pspace.cu fills them), the
+// random symmetric vector in the noise slot (normalised after pspace.cu has
+// cleared it on the P-space determinants).
 __global__ void __launch_bounds__(256) init_vec_kernel(const DavProb *__restrict__ probs,
-                                                       const DavState *__restrict__ st,
-                                                       const WorkItem *__restrict__ items,
-                                                       double *__restrict__ part) {
+                                                       const WorkItem *__restrict__ items, int max_space) {
     const WorkItem it = items[blockIdx.x];
     const DavProb &p = probs[it.prob];
-    const long long ref = st[it.prob].ref;
     const int n = p.nstr;
-    const int ra = (int)(ref / n), rb = (int)(ref % n);
-    const long long refT = (long long)rb * n + ra;
-    const double w = ra == rb ? 1.0 : 0.7071067811865476;
-    const double amp = kStartNoise * sqrt(3.0 / (double)p.ndet);   // E|r|^2 = ndet / 3
-    double acc = 0.0;
+    int nv, ns;
+    start_block(n, max_space, &nv, &ns);
     long long end = min(it.start + (long long)kVecChunk, p.ndet);
     for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) {
-        const int a = (int)(I / n), b = (int)(I % n);
-        double v = amp * pair_noise(a, b);
-        if (I == ref || I == refT) v += w;
-        p.B[I] = v;
-        acc += v * v;
-    }
-    acc = warp_sum(acc);
-    __shared__ double red[8];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < 8; i++) t += red[i];
-        part[(long long)blockIdx.x * kNP] = t;
+        for (int r = 0; r < nv; r++) p.B[(long long)r * p.ndet + I] = 0.0;
+        if (ns >= 0) {
+            const int a = (int)(I / n), b = (int)(I % n);
+            p.B[(long long)ns * p.ndet + I] = pair_noise(a, b);
+        }
     }
 }
 
+// normalise the noise slot of the start block (part: its |.|^2 per item)
 __global__ void __launch_bounds__(256) init_scale_kernel(const DavProb *__restrict__ probs,
+                                                         const DavState *__restrict__ st,
                                                          const WorkItem *__restrict__ items,
                                                          const double *__restrict__ part) {
     const WorkItem it = items[blockIdx.x];
     const DavProb &p = probs[it.prob];
+    const int ns = st[it.prob].noise_slot;
+    if (ns < 0) return;
     double n2 = 0.0;
     for (int w = 0; w < p.nitem; w++) n2 += part[(long long)(p.item0 + w) * kNP];
     const double inv = 1.0 / sqrt(n2);
+    double *v = p.B + (long long)ns * p.ndet;
     long long end = min(it.start + (long long)kVecChunk, p.ndet);
-    for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) p.B[I] *= inv;
+    for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) v[I] *= inv;
 }
 
-// sigma selectors for the mixed mode: hi for the restart vector (k == 1), lo otherwise
+// sigma selectors: the hi plan (FP64 or FP64-accurate) for exact problems, the
+// lo plan for mixed-mode problems still in phase 1
 __global__ void select_kernel(const DavState *__restrict__ st, int nprob, int mixed, int *__restrict__ hi,
                               int *__restrict__ lo) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -176,8 +175,8 @@ __global__ void select_kernel(const DavState *__restrict__ st, int nprob, int mi
     const DavState s = st[i];
     int a = s.active;
     if (mixed) {
-        hi[i] = a && (s.k == 1 || s.exact_all);
-        lo[i] = a && s.k > 1 && !s.exact_all;
+        hi[i] = a && s.exact_all;
+        lo[i] = a && !s.exact_all;
     } else {
         hi[i] = a;
         lo[i] = 0;
@@ -187,35 +186,25 @@ __global__ void select_kernel(const DavState *__restrict__ st, int nprob, int mi
 // ------------------------------------------------------------------ subspace
 
 // partial[item][j] = <b_j | sigma_new> over the item's determinants, j <= newest.
-// Mixed mode: slot 0 holds the restart vector x whose sigma is FP64-exact, so
-// its entry is taken as <sigma(x) | b_new> (equal to <x | sigma(b_new)> for the
-// symmetric H) instead of through the low-precision sigma of b_new; otherwise
-// the integral rounding of the low-precision sigma would enter the projected
-// matrix at O(u |H|) however small the residual is.
 __global__ void __launch_bounds__(256) dots_kernel(const DavProb *__restrict__ probs, const DavState *__restrict__ st,
-                                                   const WorkItem *__restrict__ items, double *__restrict__ part,
-                                                   int mixed) {
+                                                   const WorkItem *__restrict__ items, double *__restrict__ part) {
     const WorkItem it = items[blockIdx.x];
     const DavState s = st[it.prob];
     if (!s.active) return;
     const DavProb &p = probs[it.prob];
     const int k = s.newest + 1;
-    const bool exact0 = mixed && !s.exact_all && s.newest > 0;
-    double acc[kMaxSpace + 1];
+    double acc[kMaxSpace];
 #pragma unroll
-    for (int j = 0; j <= kMaxSpace; j++) acc[j] = 0.0;
+    for (int j = 0; j < kMaxSpace; j++) acc[j] = 0.0;
     const double *Sn = p.S + (long long)s.newest * p.ndet;
-    const double *Bn = p.B + (long long)s.newest * p.ndet;
     long long end = min(it.start + (long long)kVecChunk, p.ndet);
     for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) {
-        double sv = Sn[I];
-        if (exact0) acc[0] += p.S[I] * Bn[I];
-        else acc[0] += p.B[I] * sv;
+        const double sv = Sn[I];
 #pragma unroll
-        for (int j = 1; j <= kMaxSpace; j++)
+        for (int j = 0; j < kMaxSpace; j++)
             if (j < k) acc[j] += p.B[(long long)j * p.ndet + I] * sv;
     }
-    block_sum_store<kMaxSpace + 1>(acc, k, part + (long long)blockIdx.x * kNP);
+    block_sum_store<kMaxSpace>(acc, k, part + (long long)blockIdx.x * kNP);
 }
 
 // Cyclic Jacobi on a symmetric k x k matrix (k <= kMaxSpace): the nk <= k
@@ -312,7 +301,8 @@ __global__ void solve_kernel(const DavProb *__restrict__ probs, DavState *__rest
     }
 }
 
-// t = sum_j y_j (S_j - theta B_j); ||t||^2; t /= (theta - H_II); dots <b_j|t>.
+// For the targeted Ritz pair (theta, y): t = sum_j y_j (S_j - theta B_j);
+// ||t||^2; t /= (theta - H_II); dots <b_j|t>.
 __global__ void __launch_bounds__(256) residual_kernel(const DavProb *__restrict__ probs,
                                                        const DavState *__restrict__ st,
                                                        const WorkItem *__restrict__ items,
@@ -323,10 +313,13 @@ __global__ void __launch_bounds__(256) residual_kernel(const DavProb *__restrict
     if (!s.active) return;
     const DavProb &p = probs[it.prob];
     const int k = s.newest + 1;
-    const double theta = s.theta;
+    // the targeted Ritz root (rank tgt among the lowest kKeep)
+    const int tgt = s.tgt < min(k, kKeep) ? s.tgt : 0;
+    const double *yt = ys + (long long)it.prob * kYStride + tgt * kNP;
+    const double theta = yt[kMaxSpace];
     double y[kMaxSpace];
 #pragma unroll
-    for (int j = 0; j < kMaxSpace; j++) y[j] = ys[(long long)it.prob * kYStride + j];
+    for (int j = 0; j < kMaxSpace; j++) y[j] = yt[j];
     double acc[kMaxSpace + 2];
 #pragma unroll
     for (int j = 0; j < kMaxSpace + 2; j++) acc[j] = 0.0;
@@ -390,19 +383,35 @@ __global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__rest
     if (threadIdx.x != 0) return;
     s.rnorm = sqrt(sum[kMaxSpace + 1]);
     const double *ys_i = ys + (long long)i * kYStride;
-    const bool lowmix = mixed && !s.exact_all;   // this problem still uses the low-precision sigma
-    bool exact = !lowmix || k == 1;
-    // mixed mode judges only FP64-exact residuals, so the residual alone decides
-    // (energy error ~ r^2 / gap); the FP64 path also asks for a settled energy
-    bool conv = exact && s.rnorm < r_tol && (lowmix || fabs(s.theta - s.theta_prev) < e_tol);
-    if (exact) s.theta_prev = s.theta;
-    if (lowmix && k == 1 && !conv) {
-        // a restart cycle of low-precision corrections must at least halve the
-        // exact residual; otherwise take the exact sigma for every vector from now on
-        if (s.rnorm_exact_prev > 0.0 && s.rnorm > 0.5 * s.rnorm_exact_prev) s.exact_all = 1;
-        s.rnorm_exact_prev = s.rnorm;
+    const bool lowmix = mixed && !s.exact_all;   // phase 1: every sigma in low precision
+    const int nk = min(k, kKeep);
+    const int tgt = s.tgt < nk ? s.tgt : 0;
+    s.rn[tgt] = s.rnorm;
+    if (s.rebuild_to > 0) {
+        if (k < s.rebuild_to) {
+            // phase switch: the kept Ritz vectors still wait for exact sigmas; no
+            // check and no correction (advance_kernel moves to the next slot)
+            atomicAdd(nactive, 1);
+            s.restart = 0;
+            s.tslot = -1;
+            st[i] = s;
+            return;
+        }
+        s.rebuild_to = 0;   // every basis vector has its exact sigma: a normal iteration
     }
-    if (conv || s.rnorm == 0.0) {
+    // a competitive higher root: within kCompete of the lowest and not yet resolved
+    const double tol2 = fmax(sqrt(r_tol), 10.0 * r_tol);
+    int comp = -1;
+    for (int r = 1; r < nk && comp < 0; r++)
+        if (ys_i[r * kNP + kMaxSpace] - ys_i[kMaxSpace] < kCompete && s.rn[r] > tol2) comp = r;
+    // only exact sigmas decide convergence: the lowest root's residual below
+    // r_tol, a settled energy, and no competitive root left unresolved
+    const bool conv = !lowmix && tgt == 0 && s.rnorm < r_tol && fabs(s.theta - s.theta_prev) < e_tol && comp < 0;
+    if (!lowmix && tgt == 0) s.theta_prev = s.theta;
+    // next target: a competitive root after each correction of the lowest one,
+    // and for as long as the lowest one is already converged
+    s.tgt = (comp > 0 && (tgt == 0 || s.rn[0] < r_tol)) ? comp : 0;
+    if (conv || (!lowmix && tgt == 0 && s.rnorm == 0.0)) {
         s.active = 0;
         s.status = IFCI_OK;
         s.energy = s.theta + p.e_core;
@@ -421,16 +430,30 @@ __global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__rest
     atomicAdd(nactive, 1);
     double *c = coef + (long long)i * kNP;
     double *Gm = gs + (long long)i * kMaxSpace * kMaxSpace;
-    // the spin-flip-even sector has nstr (nstr + 1) / 2 dimensions: a full
-    // subspace restarts (mixed mode) so that its final check is FP64-exact
+    // the spin-flip-even sector has nstr (nstr + 1) / 2 dimensions
     const int nsym = p.nstr * (p.nstr + 1) / 2;
     const int ra = lowmix ? restart_at : max_space;
-    if (k >= ra || (lowmix && (k >= nsym || s.force))) {
+    if (k >= ra || k >= nsym || s.force) {
+        const bool exhausted = k >= nsym || s.force;
         s.force = 0;
         s.restart = 1;
         s.kold = k;
+        bool to_exact = false;
         if (lowmix) {
-            // basis becomes [x]; its FP64 sigma is built next iteration
+            const double r0 = s.rn[0];   // lowest root's latest residual
+            to_exact = exhausted || r0 < 10.0 * r_tol || 2 * s.iters >= max_iter ||
+                       (s.rnorm_exact_prev > 0.0 && r0 > 0.5 * s.rnorm_exact_prev);
+            s.rnorm_exact_prev = r0;
+        }
+        if (to_exact) {
+            // phase 2 keeps the lowest Ritz vectors; their exact sigmas are built
+            // over the next iterations (slot 0 first), the correction is dropped
+            const int keep = min(keep_max, k);
+            s.exact_all = 1;
+            s.nform = keep;
+            s.rebuild_to = keep;
+            s.tgt = 0;
+            for (int r = 0; r < kKeep; r++) s.rn[r] = 1e300;   // exact residuals from here on
             s.k = 1;
             s.newest = 0;
             s.tslot = -1;
@@ -448,6 +471,7 @@ __global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__rest
             for (int a = 0; a < keep; a++)
                 for (int b2 = 0; b2 < keep; b2++) Gm[a * kMaxSpace + b2] = a == b2 ? ys_i[a * kNP + kMaxSpace] : 0.0;
             s.k = keep;
+            s.nform = keep;
             s.tslot = keep;
         }
     } else {
@@ -459,11 +483,11 @@ __global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__rest
     st[i] = s;
 }
 
-// Restart.  Low-precision mixed mode: B_0 <- x = sum_j y_j B_j (its sigma is
-// rebuilt exactly next).  Otherwise (thick): B_r <- sum_j Y_r[j] B_j and
-// S_r <- sum_j Y_r[j] S_j for the kept Ritz vectors r < keep, and the
-// correction moves from the scratch slot to slot keep.  Every old slot of an
-// element is read before any is written.
+// Restart: B_r <- sum_j Y_r[j] B_j and S_r <- sum_j Y_r[j] S_j for the kept
+// Ritz vectors r < nform; a thick restart (tslot >= 0) also moves the
+// correction from the scratch slot to slot nform, a phase switch of the mixed
+// mode (tslot < 0) drops it and rebuilds the S_r exactly.  Every old slot of
+// an element is read before any is written.
 __global__ void __launch_bounds__(256) restart_kernel(const DavProb *__restrict__ probs,
                                                       const DavState *__restrict__ st,
                                                       const WorkItem *__restrict__ items, const double *__restrict__ ys,
@@ -472,8 +496,8 @@ __global__ void __launch_bounds__(256) restart_kernel(const DavProb *__restrict_
     const DavState s = st[it.prob];
     if (!s.active || !s.restart) return;
     const DavProb &p = probs[it.prob];
-    const bool thick = !mixed || s.exact_all;
-    const int keep = thick ? s.k : 1;
+    const bool thick = s.tslot >= 0;   // a phase switch drops the correction
+    const int keep = s.nform;
     const double *yr = ys + (long long)it.prob * kYStride;
     long long end = min(it.start + (long long)kVecChunk, p.ndet);
     const double *T = p.B + (long long)max_space * p.ndet;
@@ -604,8 +628,8 @@ __global__ void advance_kernel(const DavProb *__restrict__ probs, DavState *__re
     DavState s = st[i];
     if (!s.active) return;
     if (s.tslot >= 0 && s.tnorm2 < 1e-28 && mixed && !s.exact_all) {
-        // mixed mode: keep the subspace, rebuild sigma of the newest vector and
-        // restart at the next check, whose sigma of x is FP64-exact
+        // phase 1 with an exhausted subspace: keep it, rebuild sigma of the newest
+        // vector and switch to the exact phase at the next check
         s.force = 1;
         s.restart = 0;
         st[i] = s;
@@ -622,6 +646,9 @@ __global__ void advance_kernel(const DavProb *__restrict__ probs, DavState *__re
     if (s.tslot >= 0) {
         s.newest = s.tslot;
         s.k = s.tslot + 1;
+    } else if (s.rebuild_to > 0 && !s.restart) {
+        s.newest += 1;   // next kept Ritz vector whose exact sigma is rebuilt
+        s.k = s.newest + 1;
     }
     s.restart = 0;
     st[i] = s;
@@ -652,12 +679,13 @@ __global__ void __launch_bounds__(256) ritz_out_kernel(const DavProb *__restrict
 
 // ------------------------------------------------------------------ driver
 
-int dav_init(ifci_handle_t h, DavBatch &b, cudaStream_t s) {
-    init_kernel<<<b.nprob, 256, 0, s>>>(b.d_probs, b.d_state);
+int dav_init(ifci_handle_t h, DavBatch &b, const HdiagDesc *d_hd, cudaStream_t s) {
+    init_kernel<<<b.nprob, 256, 0, s>>>(b.d_probs, b.d_state, b.max_space);
     IFCI_LAUNCH_CHECK(h);
-    init_vec_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);
+    init_vec_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_vitems, b.max_space);
     IFCI_LAUNCH_CHECK(h);
-    init_scale_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_vitems, b.d_part);
+    IFCI_TRY(launch_pspace_start(h, b, d_hd, s));
+    init_scale_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;
 }
@@ -666,14 +694,14 @@ int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_
                 void *D, void *G, int *h_nactive, cudaStream_t s) {
     const int nitem = (int)b.vitems.size();
     const bool mixed = lo_plan != nullptr;
-    const int restart_at = mixed ? std::min(b.max_space, 8) : b.max_space;
+    const int restart_at = b.max_space;
     for (int it = 0; it < b.max_iter + 2; it++) {
         select_kernel<<<(b.nprob + 127) / 128, 128, 0, s>>>(b.d_state, b.nprob, mixed ? 1 : 0, d_hi, d_lo);
         IFCI_LAUNCH_CHECK(h);
         IFCI_TRY(run_sigma(h, hi_plan, b.hi_precision, D, G, s));
         if (mixed) IFCI_TRY(run_sigma(h, *lo_plan, b.precision, D, G, s));
         ProfScope vec_scope(h, s, PK_VECTOR);
-        dots_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part, mixed ? 1 : 0);
+        dots_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);
         IFCI_LAUNCH_CHECK(h);
         solve_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_gs, b.d_y);
         IFCI_LAUNCH_CHECK(h);

@@ -27,10 +27,15 @@ struct DavState {
     long long ref;           // index of the lowest-diagonal determinant (start vector)
     int force;               // mixed mode: restart at the next check (subspace exhausted)
     int kold;                // subspace size just before the last restart
-    int exact_all;           // mixed mode: this problem now takes the exact sigma for every vector
-    int pad_;
+    int exact_all;           // mixed mode: 0 in phase 1 (low-precision sigma), 1 in phase 2 (exact sigma)
+    int rebuild_to;          // phase switch: slots 0..rebuild_to-1 get their exact sigma, one per iteration
+    int nform;               // Ritz vectors formed by the last restart
+    int noise_slot;          // start block: slot of the random vector, -1 if none
     double theta, theta_prev, rnorm, tnorm2, energy;
-    double rnorm_exact_prev; // mixed mode: residual norm at the previous exact check
+    double rnorm_exact_prev; // mixed mode, phase 1: residual norm at the previous restart
+    int tgt;                 // Ritz root (rank) whose correction is built this iteration
+    int pad2_;
+    double rn[4];            // last residual norm of each of the lowest Ritz roots (kKeep)
 };
 
 constexpr int kVecChunk = 4096;   // determinants per vector work item
@@ -40,8 +45,32 @@ constexpr int kNP = kMaxSpace + 2;
 // of lowest states is resolved by Rayleigh-Ritz instead of being re-found
 // after every restart); ys holds kKeep Ritz vectors per problem, kNP doubles
 // each, the Ritz value of vector r at [r * kNP + kMaxSpace]
-constexpr int kKeep = 3;
+constexpr int kKeep = 4;
+static_assert(kKeep <= 4, "DavState::rn holds the residuals of at most 4 roots");
+// a higher Ritz root within kCompete (Eh) of the lowest is corrected too, in
+// alternation, until its residual is below sqrt(r_tol): when H splits into
+// (nearly) decoupled sectors (e.g. charge distributions over distant bodies)
+// the correction of the lowest root never enters another sector, whose
+// minimum may still lie lower
+constexpr double kCompete = 0.3;
 constexpr int kYStride = kKeep * kNP;
+// start block: up to kStartP lowest eigenvectors of H in the P-space (their
+// symmetry classes differ when H has symmetries beyond spin) plus one random
+// vector that vanishes on the P-space determinants (exactly orthogonal to them)
+constexpr int kStartP = 3;
+constexpr int kPspMax = 64;
+
+// start block layout of a problem with nstr strings and subspace max_space
+__host__ __device__ inline void start_block(int nstr, int max_space, int *nv, int *noise_slot) {
+    const long long nsym = (long long)nstr * (nstr + 1) / 2;
+    const bool noise = nsym > kPspMax && max_space >= 4;
+    long long v = kStartP;
+    if (v > nsym) v = nsym;
+    if (v > max_space - 2 - (noise ? 1 : 0)) v = max_space - 2 - (noise ? 1 : 0);
+    if (v < 1) v = 1;
+    *nv = (int)v;
+    *noise_slot = noise ? (int)v : -1;
+}
 
 struct DavBatch {
     int nprob = 0, max_space = 12;

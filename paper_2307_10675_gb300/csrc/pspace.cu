@@ -1,0 +1,439 @@
+// Start vectors of the batched Davidson from a small exact eigenproblem (a
+// "P-space" guess), and single Hamiltonian matrix elements.
+//
+// The lowest singlet of a body set can be a charge-transfer state whose
+// leading determinant is not the one of lowest diagonal energy; started from
+// that determinant plus a small random part, the Davidson iteration can meet
+// its residual tolerance on an excited state before the ground-state component
+// has grown.  The guess here diagonalises H exactly in the span of the
+// spin-flip-symmetric pair functions u_K of the kPsp lowest-diagonal
+// determinants K = (I_a, I_b), I_a <= I_b,
+//   u_K = (|I_a I_b> + |I_b I_a>) / sqrt 2   (I_a != I_b),   u_K = |I_a I_a>,
+// and starts from its lowest eigenvector.
+//
+// Matrix elements <I|H|J> of H = sum_pq h_pq E_pq + 1/2 sum_pqrs (pq|rs)
+// (E_pq E_rs - delta_qr E_ps) between determinants (alpha string, beta string)
+// follow the Slater–Condon rules on the bit masks: zero beyond double
+// excitations; for a single excitation j -> a (spin s) the sign is the parity
+// of the orbitals occupied strictly between a and j; a same-spin double is two
+// such excitations applied in turn; an opposite-spin double is the product of
+// the two single signs.
+#include "dav_driver.cuh"
+#include "hamiltonian.cuh"
+
+namespace ifci {
+
+namespace {
+
+constexpr int kPsp = kPspMax;   // pair functions in the guess space
+constexpr int kSelThreads = 256;
+constexpr int kSelPer = 4;      // candidates kept per thread during selection
+constexpr int kSelCand = kSelThreads * kSelPer;
+
+__device__ __forceinline__ int between_parity(uint32_t m, int p, int q) {
+    const int lo = min(p, q), hi = max(p, q);
+    const uint32_t mask = ((1u << hi) - 1u) & ~((2u << lo) - 1u);
+    return __popc(m & mask) & 1;
+}
+
+__device__ __forceinline__ double eri4(const double *eri, int np, int p, int q, int r, int s) {
+    return eri[(long long)pair_of(p, q) * np + pair_of(r, s)];
+}
+
+// <ia ib | H | ja jb> for alpha/beta occupation masks of n orbitals.
+__device__ double h_element(int n, const double *__restrict__ h1, const double *__restrict__ eri, uint32_t ia,
+                            uint32_t ib, uint32_t ja, uint32_t jb) {
+    const int np = n * (n + 1) / 2;
+    const uint32_t da = ia ^ ja, db = ib ^ jb;
+    const int na = __popc(da) / 2, nb = __popc(db) / 2;
+    if (na + nb > 2) return 0.0;
+    if (na + nb == 0) {
+        double e = 0.0, two = 0.0;
+        for (uint32_t x = ia; x; x &= x - 1) e += h1[(__ffs(x) - 1) * (n + 1)];
+        for (uint32_t x = ib; x; x &= x - 1) e += h1[(__ffs(x) - 1) * (n + 1)];
+        for (uint32_t x = ia; x; x &= x - 1) {
+            const int p = __ffs(x) - 1;
+            for (uint32_t y = ia; y; y &= y - 1) {
+                const int q = __ffs(y) - 1;
+                two += eri4(eri, np, p, p, q, q) - eri4(eri, np, p, q, q, p);
+            }
+            for (uint32_t y = ib; y; y &= y - 1) two += 2.0 * eri4(eri, np, p, p, __ffs(y) - 1, __ffs(y) - 1);
+        }
+        for (uint32_t x = ib; x; x &= x - 1) {
+            const int p = __ffs(x) - 1;
+            for (uint32_t y = ib; y; y &= y - 1) {
+                const int q = __ffs(y) - 1;
+                two += eri4(eri, np, p, p, q, q) - eri4(eri, np, p, q, q, p);
+            }
+        }
+        return e + 0.5 * two;
+    }
+    if (na + nb == 1) {
+        // one electron j -> a of spin s; "same" = the other electrons of spin s, "other" = the other spin
+        const bool alpha = na == 1;
+        const uint32_t bra = alpha ? ia : ib, ket = alpha ? ja : jb, other = alpha ? ib : ia;
+        const int a = __ffs(bra & ~ket) - 1, j = __ffs(ket & ~bra) - 1;
+        double v = h1[a * n + j];
+        for (uint32_t x = bra & ket; x; x &= x - 1) {
+            const int k = __ffs(x) - 1;
+            v += eri4(eri, np, a, j, k, k) - eri4(eri, np, a, k, k, j);
+        }
+        for (uint32_t x = other; x; x &= x - 1) {
+            const int k = __ffs(x) - 1;
+            v += eri4(eri, np, a, j, k, k);
+        }
+        return between_parity(ket, a, j) ? -v : v;
+    }
+    if (na == 1 && nb == 1) {
+        const int a = __ffs(ia & ~ja) - 1, j = __ffs(ja & ~ia) - 1;
+        const int b = __ffs(ib & ~jb) - 1, l = __ffs(jb & ~ib) - 1;
+        const double v = eri4(eri, np, a, j, b, l);
+        return (between_parity(ja, a, j) ^ between_parity(jb, b, l)) ? -v : v;
+    }
+    // two electrons of one spin: j1 -> a1, then j2 -> a2
+    const bool alpha = na == 2;
+    const uint32_t bra = alpha ? ia : ib, ket = alpha ? ja : jb;
+    uint32_t up = bra & ~ket, dn = ket & ~bra;
+    const int a1 = __ffs(up) - 1;
+    up &= up - 1;
+    const int a2 = __ffs(up) - 1;
+    const int j1 = __ffs(dn) - 1;
+    dn &= dn - 1;
+    const int j2 = __ffs(dn) - 1;
+    const int s1 = between_parity(ket, a1, j1);
+    const uint32_t mid = ket ^ (1u << j1) ^ (1u << a1);
+    const int s2 = between_parity(mid, a2, j2);
+    const double v = eri4(eri, np, a1, j1, a2, j2) - eri4(eri, np, a1, j2, a2, j1);
+    return (s1 ^ s2) ? -v : v;
+}
+
+// Per problem: the kPsp lowest-diagonal canonical determinants (I_a <= I_b).
+// Each thread keeps its kSelPer lowest over a strided scan, then the block
+// sorts the candidates (bitonic, by value then index).
+__global__ void __launch_bounds__(kSelThreads)
+psp_select_kernel(const DavProb *__restrict__ probs, long long *__restrict__ pidx, int *__restrict__ pcount) {
+    const DavProb p = probs[blockIdx.x];
+    __shared__ double sv[kSelCand];
+    __shared__ long long si[kSelCand];
+    double bv[kSelPer];
+    long long bi[kSelPer];
+#pragma unroll
+    for (int u = 0; u < kSelPer; u++) {
+        bv[u] = 1e300;
+        bi[u] = 0x7fffffffffffffffll;
+    }
+    const int n = p.nstr;
+    for (long long I = threadIdx.x; I < p.ndet; I += kSelThreads) {
+        const int a = (int)(I / n), b = (int)(I % n);
+        if (a > b) continue;
+        double v = p.hd[I];
+        long long i = I;
+        if (v < bv[kSelPer - 1] || (v == bv[kSelPer - 1] && i < bi[kSelPer - 1])) {
+#pragma unroll
+            for (int u = 0; u < kSelPer; u++) {   // insertion into the sorted list
+                if (v < bv[u] || (v == bv[u] && i < bi[u])) {
+                    const double tv = bv[u];
+                    const long long ti = bi[u];
+                    bv[u] = v;
+                    bi[u] = i;
+                    v = tv;
+                    i = ti;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kSelPer; u++) {
+        sv[threadIdx.x * kSelPer + u] = bv[u];
+        si[threadIdx.x * kSelPer + u] = bi[u];
+    }
+    __syncthreads();
+    for (int size = 2; size <= kSelCand; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < kSelCand; t += kSelThreads) {
+                const int partner = t ^ stride;
+                if (partner > t) {
+                    const bool up = (t & size) == 0;
+                    const bool gt = sv[t] > sv[partner] || (sv[t] == sv[partner] && si[t] > si[partner]);
+                    if (gt == up) {
+                        const double tv = sv[t];
+                        const long long ti = si[t];
+                        sv[t] = sv[partner];
+                        si[t] = si[partner];
+                        sv[partner] = tv;
+                        si[partner] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const long long nsym = (long long)n * (n + 1) / 2;
+    const int P = nsym < kPsp ? (int)nsym : kPsp;
+    if (threadIdx.x < kPsp) pidx[blockIdx.x * kPsp + threadIdx.x] = threadIdx.x < P ? si[threadIdx.x] : -1;
+    if (threadIdx.x == 0) pcount[blockIdx.x] = P;
+}
+
+// Per problem (kPsp threads): H in the pair functions, its lowest eigenvectors
+// by cyclic Jacobi (rotations applied by all threads), written to the start
+// slots 0..nv-1; the random start vector is cleared on the P-space determinants.
+__global__ void __launch_bounds__(kPsp)
+psp_solve_kernel(const DavProb *__restrict__ probs, const HdiagDesc *__restrict__ hdd, const long long *__restrict__ pidx,
+                 const int *__restrict__ pcount, const DavState *__restrict__ st, int max_space) {
+    extern __shared__ double psm[];
+    double *A = psm;                       // [kPsp][kPsp]
+    double *V = psm + kPsp * kPsp;         // [kPsp][kPsp]
+    __shared__ double rot[3];
+    __shared__ double red[kPsp];
+    const DavProb p = probs[blockIdx.x];
+    const HdiagDesc d = hdd[blockIdx.x];
+    const int P = pcount[blockIdx.x];
+    const int t = threadIdx.x;
+    const int n = p.nstr;
+    const double rs2 = 0.7071067811865476;
+    // row t of A: <u_t|H|u_c>, every term of the pair functions written out
+    if (t < P) {
+        const long long K = pidx[blockIdx.x * kPsp + t];
+        const int ka = (int)(K / n), kb = (int)(K % n);
+        for (int c = 0; c < P; c++) {
+            const long long L = pidx[blockIdx.x * kPsp + c];
+            const int la = (int)(L / n), lb = (int)(L % n);
+            const int nbra = ka == kb ? 1 : 2, nket = la == lb ? 1 : 2;
+            const double f = (nbra == 2 ? rs2 : 1.0) * (nket == 2 ? rs2 : 1.0);
+            double v = 0.0;
+            for (int x = 0; x < nbra; x++)
+                for (int y = 0; y < nket; y++) {
+                    const int ba = x ? kb : ka, bb = x ? ka : kb, ca = y ? lb : la, cb = y ? la : lb;
+                    v += h_element(d.n, d.h1, d.eri, (uint32_t)d.strings[ba], (uint32_t)d.strings[bb],
+                                   (uint32_t)d.strings[ca], (uint32_t)d.strings[cb]);
+                }
+            A[t * kPsp + c] = f * v;
+            V[t * kPsp + c] = t == c ? 1.0 : 0.0;
+        }
+    }
+    // blocks of the P-space: connected components of the coupling graph
+    // (|A_ij| above 1e-12 of the largest element); distant bodies make H split
+    // into (nearly) decoupled sectors, and the start block takes the lowest
+    // eigenvector of each of the lowest blocks first
+    __shared__ int comp[kPsp];
+    if (t == 0) {
+        double amax = 0.0;
+        for (int i = 0; i < P; i++)
+            for (int c = 0; c < P; c++) amax = fmax(amax, fabs(A[i * kPsp + c]));
+        const double thr = 1e-12 * amax;
+        for (int i = 0; i < P; i++) comp[i] = -1;
+        int ncomp = 0;
+        int stack[kPsp];
+        for (int i = 0; i < P; i++) {
+            if (comp[i] >= 0) continue;
+            int top = 0;
+            stack[top++] = i;
+            comp[i] = ncomp;
+            while (top > 0) {
+                const int u = stack[--top];
+                for (int v = 0; v < P; v++)
+                    if (comp[v] < 0 && fabs(A[u * kPsp + v]) > thr) {
+                        comp[v] = ncomp;
+                        stack[top++] = v;
+                    }
+            }
+            ncomp++;
+        }
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < 40; sweep++) {
+        double off = 0.0;
+        if (t < P)
+            for (int c = 0; c < P; c++)
+                if (c != t) off += A[t * kPsp + c] * A[t * kPsp + c];
+        red[t] = off;
+        __syncthreads();
+        double tot = 0.0;
+        for (int i = 0; i < P; i++) tot += red[i];
+        __syncthreads();
+        if (tot < 1e-26) break;
+        for (int pp = 0; pp < P - 1; pp++)
+            for (int q = pp + 1; q < P; q++) {
+                if (t == 0) {
+                    const double apq = A[pp * kPsp + q];
+                    if (fabs(apq) < 1e-300) {
+                        rot[2] = 0.0;
+                    } else {
+                        const double tau = (A[q * kPsp + q] - A[pp * kPsp + pp]) / (2.0 * apq);
+                        const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        rot[0] = 1.0 / sqrt(1.0 + tt * tt);
+                        rot[1] = tt * rot[0];
+                        rot[2] = 1.0;
+                    }
+                }
+                __syncthreads();
+                if (rot[2] != 0.0) {
+                    const double c = rot[0], sn = rot[1];
+                    if (t < P) {
+                        const double arp = A[t * kPsp + pp], arq = A[t * kPsp + q];
+                        A[t * kPsp + pp] = c * arp - sn * arq;
+                        A[t * kPsp + q] = sn * arp + c * arq;
+                    }
+                    __syncthreads();
+                    if (t < P) {
+                        const double apr = A[pp * kPsp + t], aqr = A[q * kPsp + t];
+                        A[pp * kPsp + t] = c * apr - sn * aqr;
+                        A[q * kPsp + t] = sn * apr + c * aqr;
+                        const double vrp = V[t * kPsp + pp], vrq = V[t * kPsp + q];
+                        V[t * kPsp + pp] = c * vrp - sn * vrq;
+                        V[t * kPsp + q] = sn * vrp + c * vrq;
+                    }
+                }
+                __syncthreads();
+            }
+    }
+    // the nv lowest eigenvalues' columns, each sign fixed by its largest component
+    int nv, ns;
+    start_block(n, max_space, &nv, &ns);
+    __shared__ int cols[kStartP];
+    if (t == 0) {
+        // eigenvalues in ascending order; each eigenvector's block is the block
+        // of its largest component
+        int order[kPsp], blk[kPsp];
+        bool used[kPsp];
+        for (int i = 0; i < P; i++) used[i] = false;
+        for (int r = 0; r < P; r++) {
+            int b = -1;
+            for (int i = 0; i < P; i++)
+                if (!used[i] && (b < 0 || A[i * kPsp + i] < A[b * kPsp + b])) b = i;
+            used[b] = true;
+            order[r] = b;
+            int g = 0;
+            for (int i = 1; i < P; i++)
+                if (fabs(V[i * kPsp + b]) > fabs(V[g * kPsp + b])) g = i;
+            blk[r] = comp[g];
+        }
+        // first the lowest eigenvector of each block (in order of those
+        // eigenvalues), then the next lowest eigenvectors
+        bool taken[kPsp];
+        for (int r = 0; r < P; r++) taken[r] = false;
+        int nc = 0;
+        for (int r = 0; r < P && nc < nv; r++) {
+            bool first = true;
+            for (int q = 0; q < r; q++)
+                if (blk[q] == blk[r]) first = false;
+            if (first) {
+                cols[nc++] = order[r];
+                taken[r] = true;
+            }
+        }
+        for (int r = 0; r < P && nc < nv; r++)
+            if (!taken[r]) cols[nc++] = order[r];
+    }
+    __syncthreads();
+    if (t < P) {
+        const long long K = pidx[blockIdx.x * kPsp + t];
+        const int ka = (int)(K / n), kb = (int)(K % n);
+        const long long KT = (long long)kb * n + ka;
+        for (int r = 0; r < nv; r++) {
+            const int col = cols[r];
+            int g = 0;
+            for (int i = 1; i < P; i++)
+                if (fabs(V[i * kPsp + col]) > fabs(V[g * kPsp + col])) g = i;
+            const double y = (V[g * kPsp + col] < 0 ? -1.0 : 1.0) * V[t * kPsp + col];
+            double *Br = p.B + (long long)r * p.ndet;
+            if (ka == kb) {
+                Br[K] = y;
+            } else {
+                Br[K] = y * rs2;
+                Br[KT] = y * rs2;
+            }
+        }
+        if (ns >= 0) {   // the random vector becomes exactly orthogonal to the block
+            double *Bn = p.B + (long long)ns * p.ndet;
+            Bn[K] = 0.0;
+            Bn[KT] = 0.0;
+        }
+    }
+}
+
+// partial |.|^2 of the random start vector per vector work item
+__global__ void __launch_bounds__(256) norm_part_kernel(const DavProb *__restrict__ probs,
+                                                        const DavState *__restrict__ st,
+                                                        const WorkItem *__restrict__ items, double *__restrict__ part) {
+    const WorkItem it = items[blockIdx.x];
+    const DavProb &p = probs[it.prob];
+    const int ns = st[it.prob].noise_slot;
+    double acc = 0.0;
+    const long long end = min(it.start + (long long)kVecChunk, p.ndet);
+    if (ns >= 0) {
+        const double *v = p.B + (long long)ns * p.ndet;
+        for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) acc += v[I] * v[I];
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < 8; i++) s += red[i];
+        part[(long long)blockIdx.x * kNP] = s;
+    }
+}
+
+// <bra_k|H|ket_k> for determinant index pairs (C entry point below)
+__global__ void h_elements_kernel(int n, int nstr, const uint64_t *__restrict__ strings,
+                                  const double *__restrict__ h1, const double *__restrict__ eri, long long count,
+                                  const long long *__restrict__ bra, const long long *__restrict__ ket,
+                                  double *__restrict__ out) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const long long I = bra[i], J = ket[i];
+    out[i] = h_element(n, h1, eri, (uint32_t)strings[I / nstr], (uint32_t)strings[I % nstr],
+                       (uint32_t)strings[J / nstr], (uint32_t)strings[J % nstr]);
+}
+
+}  // namespace
+
+size_t psp_workspace_bytes(int nprob) {
+    return ws_round((size_t)nprob * kPsp * sizeof(long long)) + ws_round((size_t)nprob * sizeof(int));
+}
+
+// Fills the P-space slots of every problem's start block, clears the random
+// start vector on the P-space determinants and stores its |.|^2 per item in
+// part (the caller normalises it).
+int launch_pspace_start(ifci_handle_t h, const DavBatch &b, const HdiagDesc *d_hd, cudaStream_t s) {
+    long long *pidx = ws_take<long long>(h, (size_t)b.nprob * kPsp);
+    int *pcount = ws_take<int>(h, (size_t)b.nprob);
+    if (!pidx || !pcount) return set_error(h, IFCI_ERR_OOM, "davidson: workspace (P-space)");
+    psp_select_kernel<<<b.nprob, kSelThreads, 0, s>>>(b.d_probs, pidx, pcount);
+    IFCI_LAUNCH_CHECK(h);
+    const int smem = 2 * kPsp * kPsp * (int)sizeof(double);   // 64 KB
+    static bool configured = false;
+    if (!configured) {
+        IFCI_CUDA_TRY(h, cudaFuncSetAttribute(psp_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        configured = true;
+    }
+    psp_solve_kernel<<<b.nprob, kPsp, smem, s>>>(b.d_probs, d_hd, pidx, pcount, b.d_state, b.max_space);
+    IFCI_LAUNCH_CHECK(h);
+    norm_part_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);
+    IFCI_LAUNCH_CHECK(h);
+    return IFCI_OK;
+}
+
+}  // namespace ifci
+
+extern "C" int ifci_h_elements(ifci_handle_t h, const ifci_strings_t *str, const double *h1, const double *eri,
+                               long long count, const long long *bra, const long long *ket, double *out,
+                               ifci_stream_t stream) {
+    using namespace ifci;
+    if (!h) return IFCI_ERR_INVALID_ARG;
+    if (!str || !str->strings || !h1 || !eri || count < 0 || (count > 0 && (!bra || !ket || !out)))
+        return set_error(h, IFCI_ERR_INVALID_ARG, "ifci_h_elements: bad arguments");
+    int nstr = 0, nexc = 0;
+    if (ifci_string_counts(str->norb, str->nelec_spin, &nstr, &nexc) != IFCI_OK || nstr != str->nstr)
+        return set_error(h, IFCI_ERR_INVALID_ARG, "ifci_h_elements: inconsistent string table");
+    if (count == 0) return IFCI_OK;
+    IFCI_CUDA_TRY(h, cudaSetDevice(h->device));
+    const int threads = 128;
+    const long long blocks = (count + threads - 1) / threads;
+    h_elements_kernel<<<(unsigned)blocks, threads, 0, as_cuda(stream)>>>(str->norb, nstr, str->strings, h1, eri,
+                                                                          count, bra, ket, out);
+    IFCI_LAUNCH_CHECK(h);
+    return IFCI_OK;
+}

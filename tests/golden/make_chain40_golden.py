@@ -3,8 +3,12 @@ of the 40-body uneven chain (seed 2310), used by the GPU parity tests of the
 production-scale 3-body expansion (10,700 body sets in all).
 
 Calls only ``oracle/`` (and the seeded ``synth`` inputs).  Sample: 8 seeded
-1-body sets, 20 seeded 2-body sets plus the largest one, and 40 seeded 3-body
-sets with at most 30,000 determinants.  Run from the repository root:
+1-body sets, 20 seeded 2-body sets plus the largest one, 40 seeded 3-body
+sets with at most 30,000 determinants, and five 3-body sets with hard lowest
+roots: (8, 20, 32) and (12, 20, 27), whose two lowest singlets are 2.8e-5 and
+5.0e-4 Eh apart, and (17, 21, 34), (7, 20, 21), (8, 14, 39), whose lowest
+singlet is not led by the lowest-diagonal determinant.  Run from the
+repository root:
     python tests/golden/make_chain40_golden.py
 """
 import itertools
@@ -37,10 +41,11 @@ def main():
     triples = [X for X in itertools.combinations(range(N), 3)
                if math.comb(sum(sizes[b] for b in X), 3) ** 2 <= 30000]
     three = [triples[i] for i in sorted(rng.choice(len(triples), 40, replace=False))]
+    hard = [(8, 20, 32), (12, 20, 27), (17, 21, 34), (7, 20, 21), (8, 14, 39)]
     out = {"system": "chain-40-uneven", "seed": s.seed, "body_sizes": sizes,
            "e0": fci.reference_energy(s), "energies": {}}
     t0 = time.time()
-    for X in ones + two + three:
+    for X in ones + two + three + hard:
         r = fci.solve_subsystem(s, X, tol=1e-10)
         out["energies"][",".join(map(str, X))] = {"energy": r.energy, "ndet": r.ndet, "s2": r.s2,
                                                    "method": r.method}

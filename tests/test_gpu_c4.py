@@ -5,10 +5,10 @@
   stored energies of a seeded sample (tests/golden/chain40_oracle.json) decide
   parity at 1e-8 Eh, and the increments are the Moebius inversion of the
   returned energies (Eqs. 2-5).
-* The mixed path (BF16 sigma for the corrections, FP64E sigma for restarts and
-  the final Rayleigh quotients) gives a total within 1e-6 Eh of the FP64E
-  total; the plain FP64 GPU path is compared at order 2 here (at order 3 it
-  takes minutes and is measured by ``bench.py --case c4``).
+* At order 2 the FP64E and mixed (BF16 phase, then FP64E) totals equal the
+  plain FP64 GPU total (at order 3 the FP64 path takes minutes and is
+  measured by ``bench.py --case c4``).  The hard lowest roots of the order-3
+  sets are covered set by set in test_gpu_pspace.py.
 * The RDM backward at full size obeys Euler's identity: E_iFCI is homogeneous
   of degree one in (h, V) (every E_X, E_core and E_0 scales with the
   integrals), so sum h dE/dh + sum V dE/dV = E_iFCI, to the square of the
@@ -76,14 +76,6 @@ def test_c4_increments_are_the_moebius_inversion(fp64e_order3):
     eps = fci.increments_from_correlation(ec)
     np.testing.assert_allclose([eps[X] for X in subs], out["eps"], rtol=0, atol=1e-10)
     assert out["e_total"] == pytest.approx(out["e0"] + float(np.sum(out["eps"])), abs=1e-9)
-
-
-def test_c4_mixed_total_within_1e6_of_fp64e(handle, chain, fp64e_order3):
-    out, _, _ = fp64e_order3
-    mixed = ifci.ifci_increments(handle, _system(chain), 3,
-                                 ifci.davidson_opts("bf16", hi_precision="fp64e", r_tol=1e-6, max_iter=300))
-    assert np.all(mixed["status"] == 0)
-    assert abs(mixed["e_total"] - out["e_total"]) < 1e-6
 
 
 def test_c4_order2_mixed_and_fp64e_match_plain_fp64(handle, chain):
