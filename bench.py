@@ -61,6 +61,16 @@ def parse():
 
 # ---------------------------------------------------------------- workload
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's time (every rank returns it); ``dist`` None = one rank."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload(rank: int = 0):
     from synth import chain_24_uneven
     # weak scaling: rank r solves its own chain (seed 2308 + r) of the same shape
@@ -264,10 +274,7 @@ def main():
         prof = handle.profile_read() if profile else None
         if profile:
             handle.profile_enable(False)
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
         return out, ms / nsteps, prof, handle.launches() - l0
 
     clocks = ClockSampler(local)
@@ -552,10 +559,7 @@ def _e2e(ifci, handle, chain, max_order, opts, world, nsub, dist, dev):
     out = ifci.ifci_increments(handle, sysh, max_order, opts)
     torch.cuda.synchronize(dev)
     el = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([el], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(el, dist, dev)
     h2d = h_pin.numel() * 8 + v_pin.numel() * 8
     d2h = (2 * nsub + 2) * 8 + nsub * 4
     return {"value": world * nsub / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
