@@ -292,6 +292,7 @@ def main():
     gelems_step = 0.0
     for (X, n, k), it in zip(subs, its):
         nd, fl = cost_of(n, k)
+        it = float(it)
         flops_step += it * fl
         exec_step += it * executed_oz_flops(n, k)
         gelems_step += it * nd * (n * (n + 1) // 2)

@@ -234,12 +234,37 @@ class Hamiltonian:
 # Eigen-solvers
 # --------------------------------------------------------------------------
 
+DEGENERATE_TOL = 1e-8      # eigenvalues closer than this form one eigenspace
+
+
 def lowest_singlet_dense(H: Hamiltonian) -> Tuple[float, np.ndarray]:
-    """Dense eigh; the lowest eigenpair whose <S^2> is below SINGLET_S2_TOL."""
+    """Dense eigh; the lowest eigenvalue whose eigenspace holds a singlet.
+
+    S^2 commutes with H, so every eigenspace has a basis of spin eigenstates,
+    but eigh returns an arbitrary basis of a degenerate eigenspace (e.g. the
+    exactly degenerate singlet and triplet of two unpaired electrons on bodies
+    that do not couple): S^2 is diagonalised inside each eigenspace, from its
+    matrix elements <v_i|S^2|v_j> (by polarisation of the expectation values),
+    and the eigenspace counts as singlet when S^2 has an eigenvalue below
+    SINGLET_S2_TOL there."""
     w, v = np.linalg.eigh(H.dense())
-    for k in range(len(w)):
-        if abs(H.s_squared(v[:, k])) < SINGLET_S2_TOL:
-            return float(w[k]), v[:, k]
+    k = 0
+    while k < len(w):
+        m = k + 1
+        while m < len(w) and w[m] - w[k] < DEGENERATE_TOL:
+            m += 1
+        V = v[:, k:m]
+        d = m - k
+        S = np.empty((d, d))
+        for i in range(d):
+            S[i, i] = H.s_squared(V[:, i])
+            for j in range(i):
+                S[i, j] = S[j, i] = 0.25 * (H.s_squared(V[:, i] + V[:, j]) - H.s_squared(V[:, i] - V[:, j]))
+        sw, sv = np.linalg.eigh(S)
+        if abs(sw[0]) < SINGLET_S2_TOL:
+            c = V @ sv[:, 0]
+            return float(w[k]), c / np.linalg.norm(c)
+        k = m
     raise RuntimeError("no singlet root found")
 
 

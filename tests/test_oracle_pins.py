@@ -180,6 +180,25 @@ def test_dense_and_lanczos_agree():
         assert abs(abs(rd.vector @ rl.vector) - 1.0) < 1e-8
 
 
+def test_degenerate_singlet_triplet_level_is_resolved():
+    """Bodies 0 and 13 of the 40-body chain sit 70 A apart (couplings
+    ~exp(-35)): the lowest level of the pair is an exactly degenerate singlet
+    and triplet (one electron moved between the bodies).  The dense solver
+    must resolve S^2 inside that eigenspace and report the level as a singlet,
+    as the Lanczos of the spin-flip-even sector does (that sector excludes
+    the triplet), and the returned vector must be a pure singlet."""
+    from synth import chain_40_uneven
+    s = chain_40_uneven()
+    H = fci.Hamiltonian(fci.subsystem(s, (0, 13)))
+    w = np.linalg.eigvalsh(H.dense())
+    assert w[1] - w[0] < 1e-8                      # the degenerate pair
+    dense = fci.solve_subsystem(s, (0, 13), "dense")
+    lan = fci.solve_subsystem(s, (0, 13), "lanczos", tol=1e-10)
+    assert dense.energy == pytest.approx(w[0], abs=1e-10)
+    assert lan.energy == pytest.approx(dense.energy, abs=1e-9)
+    assert abs(dense.s2) < 1e-8
+
+
 def test_lanczos_finds_a_charge_transfer_ground_state():
     """Two bodies with no inter-body hopping: each body's electron count is
     conserved, and the ground state lies in the charge-transfer sector (0, 4)
