@@ -183,7 +183,6 @@ psp_solve_kernel(const DavProb *__restrict__ probs, const HdiagDesc *__restrict_
     extern __shared__ double psm[];
     double *A = psm;                       // [kPsp][kPsp]
     double *V = psm + kPsp * kPsp;         // [kPsp][kPsp]
-    __shared__ double rot[3];
     __shared__ double red[kPsp];
     const DavProb p = probs[blockIdx.x];
     const HdiagDesc d = hdd[blockIdx.x];
@@ -254,35 +253,28 @@ psp_solve_kernel(const DavProb *__restrict__ probs, const HdiagDesc *__restrict_
         if (tot < 1e-26) break;
         for (int pp = 0; pp < P - 1; pp++)
             for (int q = pp + 1; q < P; q++) {
-                if (t == 0) {
-                    const double apq = A[pp * kPsp + q];
-                    if (fabs(apq) < 1e-300) {
-                        rot[2] = 0.0;
-                    } else {
-                        const double tau = (A[q * kPsp + q] - A[pp * kPsp + pp]) / (2.0 * apq);
-                        const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        rot[0] = 1.0 / sqrt(1.0 + tt * tt);
-                        rot[1] = tt * rot[0];
-                        rot[2] = 1.0;
-                    }
+                // every thread reads the same settled entries and derives the same
+                // rotation (no barrier); zero couplings (other sectors, pair
+                // functions beyond a double excitation apart) are skipped
+                const double apq = A[pp * kPsp + q];
+                if (fabs(apq) < 1e-300) continue;
+                const double tau = (A[q * kPsp + q] - A[pp * kPsp + pp]) / (2.0 * apq);
+                const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                const double c = 1.0 / sqrt(1.0 + tt * tt), sn = tt * c;
+                __syncthreads();   // every thread has read A[pp][q], A[pp][pp], A[q][q]
+                if (t < P) {
+                    const double arp = A[t * kPsp + pp], arq = A[t * kPsp + q];
+                    A[t * kPsp + pp] = c * arp - sn * arq;
+                    A[t * kPsp + q] = sn * arp + c * arq;
                 }
                 __syncthreads();
-                if (rot[2] != 0.0) {
-                    const double c = rot[0], sn = rot[1];
-                    if (t < P) {
-                        const double arp = A[t * kPsp + pp], arq = A[t * kPsp + q];
-                        A[t * kPsp + pp] = c * arp - sn * arq;
-                        A[t * kPsp + q] = sn * arp + c * arq;
-                    }
-                    __syncthreads();
-                    if (t < P) {
-                        const double apr = A[pp * kPsp + t], aqr = A[q * kPsp + t];
-                        A[pp * kPsp + t] = c * apr - sn * aqr;
-                        A[q * kPsp + t] = sn * apr + c * aqr;
-                        const double vrp = V[t * kPsp + pp], vrq = V[t * kPsp + q];
-                        V[t * kPsp + pp] = c * vrp - sn * vrq;
-                        V[t * kPsp + q] = sn * vrp + c * vrq;
-                    }
+                if (t < P) {
+                    const double apr = A[pp * kPsp + t], aqr = A[q * kPsp + t];
+                    A[pp * kPsp + t] = c * apr - sn * aqr;
+                    A[q * kPsp + t] = sn * apr + c * aqr;
+                    const double vrp = V[t * kPsp + pp], vrq = V[t * kPsp + q];
+                    V[t * kPsp + pp] = c * vrp - sn * vrq;
+                    V[t * kPsp + q] = sn * vrp + c * vrq;
                 }
                 __syncthreads();
             }
