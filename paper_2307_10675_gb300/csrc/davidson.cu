@@ -8,7 +8,8 @@
 // Vector passes of one iteration (k = subspace size):
 //   sigma(b_new) -> subspace column <b_j|sigma_new> -> k x k Jacobi eigen-solve
 //   -> residual r = sum_j y_j (sigma_j - theta b_j), correction t = r / (theta - H_II)
-//   -> classical Gram-Schmidt twice -> normalise, symmetrise (c = c^T sector).
+//   -> classical Gram-Schmidt (a second pass when the first removed more than
+//   half of |t|^2) -> normalise, symmetrise (c = c^T sector).
 //
 // A full subspace restarts thick: it keeps the lowest Ritz vectors (up to
 // kKeep, with their sigmas and a diagonal projected matrix) plus the new
@@ -530,10 +531,11 @@ __global__ void __launch_bounds__(256) restart_kernel(const DavProb *__restrict_
 __global__ void __launch_bounds__(256) ortho_kernel(const DavProb *__restrict__ probs, const DavState *__restrict__ st,
                                                     const WorkItem *__restrict__ items,
                                                     const double *__restrict__ coef, int max_space,
-                                                    double *__restrict__ part) {
+                                                    double *__restrict__ part, int pass) {
     const WorkItem it = items[blockIdx.x];
     const DavState s = st[it.prob];
     if (!s.active || s.tslot < 0) return;
+    if (pass == 1 && s.skip2) return;
     const DavProb &p = probs[it.prob];
     const int k = s.k;
     double c[kMaxSpace];
@@ -577,18 +579,27 @@ __global__ void __launch_bounds__(256) ortho_kernel(const DavProb *__restrict__ 
     }
 }
 
+// After Gram-Schmidt pass `pass`: the coefficients of the next pass and |t|^2.
+// The second pass runs only when the first one removed more than half of
+// |t|^2 (the DGKS criterion with eta = 1/sqrt 2: a first pass that kept
+// |t| >= |t_before| / sqrt 2 leaves t orthogonal to working precision).
 __global__ void reduce_coef_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st,
-                                   const double *__restrict__ part, double *__restrict__ coef) {
+                                   const double *__restrict__ part, double *__restrict__ coef, int pass) {
     const int i = blockIdx.x;
     DavState s = st[i];
     if (!s.active || s.tslot < 0) return;
+    if (pass == 1 && s.skip2) return;
     const DavProb p = probs[i];
     const int k = s.k;
     if (threadIdx.x < k || threadIdx.x == kMaxSpace) {
         double v = 0.0;
         for (int w = 0; w < p.nitem; w++) v += part[(long long)(p.item0 + w) * kNP + threadIdx.x];
-        if (threadIdx.x == kMaxSpace) st[i].tnorm2 = v;
-        else coef[(long long)i * kNP + threadIdx.x] = v;
+        if (threadIdx.x == kMaxSpace) {
+            if (pass == 0) st[i].skip2 = v >= 0.5 * s.tnorm2 ? 1 : 0;
+            st[i].tnorm2 = v;
+        } else {
+            coef[(long long)i * kNP + threadIdx.x] = v;
+        }
     }
     if (threadIdx.x > k && threadIdx.x < kMaxSpace) coef[(long long)i * kNP + threadIdx.x] = 0.0;
 }
@@ -716,9 +727,10 @@ int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_
         restart_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, mixed ? 1 : 0);
         IFCI_LAUNCH_CHECK(h);
         for (int pass = 0; pass < 2; pass++) {
-            ortho_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_coef, b.max_space, b.d_part);
+            ortho_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_coef, b.max_space, b.d_part,
+                                               pass);
             IFCI_LAUNCH_CHECK(h);
-            reduce_coef_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_coef);
+            reduce_coef_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_coef, pass);
             IFCI_LAUNCH_CHECK(h);
         }
         normalize_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.max_space);

@@ -34,7 +34,7 @@ struct DavState {
     double theta, theta_prev, rnorm, tnorm2, energy;
     double rnorm_exact_prev; // mixed mode, phase 1: residual norm at the previous restart
     int tgt;                 // Ritz root (rank) whose correction is built this iteration
-    int pad2_;
+    int skip2;               // the second Gram-Schmidt pass is not needed this iteration
     double rn[4];            // last residual norm of each of the lowest Ritz roots (kKeep)
 };
 
