@@ -92,6 +92,14 @@ size_t ifci_workspace_bytes(ifci_handle_t handle);
 /* Number of kernel launches this handle has issued since creation. */
 long long ifci_kernel_launches(ifci_handle_t handle);
 
+/* ifci_wait_selftest — makes one bounded device wait run out on purpose (a
+ * CTA waits for an mbarrier arrival that nothing makes, for limit_cycles SM
+ * clocks, 1 .. 4e9) and returns IFCI_ERR_TIMEOUT exactly as a timed-out wait
+ * inside the contraction kernels does; the CUDA context stays usable and the
+ * handle's error flag is cleared.  No paper counterpart: it exercises the
+ * library's failure detection without a GPU fault.  Synchronous. */
+int ifci_wait_selftest(ifci_handle_t handle, long long limit_cycles, ifci_stream_t stream);
+
 /* Per-kernel-class timing with CUDA events recorded on the launching stream
  * around every kernel the library issues (no paper counterpart; it serves
  * the roofline measurement).  enable != 0 turns it on and zeroes the totals.
@@ -228,6 +236,11 @@ typedef struct {
     int hi_precision;    /* mixed mode: sigma of restart vectors, IFCI_FP64 or IFCI_FP64E
                             (default IFCI_FP64E) */
     long long det_budget;/* determinants per sigma wave (0 = from workspace size) */
+    int graph_iters;     /* > 0: Davidson iterations are captured in blocks of this
+                            many into one CUDA graph, replayed on a stream of the
+                            handle (event-ordered with `stream`); 0 = launched one
+                            by one (default).  Ignored while profiling is on.
+                            Results are identical either way. */
 } ifci_davidson_opts_t;
 
 /* Fills opts with the defaults listed above (precision IFCI_FP64). */

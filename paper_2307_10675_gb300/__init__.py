@@ -9,5 +9,6 @@ from .api import (  # noqa: F401
     body_subsets, davidson_opts,
     ifci_build_strings, ifci_davidson_batched, ifci_frozen_core, ifci_h_elements, ifci_hdiag, ifci_increments,
     ifci_num_subsets, ifci_rdm_backward, ifci_sigma, ifci_sigma_noalloc, ifci_sigma_noalloc_max_bytes,
+    ifci_wait_selftest,
     ifci_string_counts,
 )

@@ -28,7 +28,7 @@ EXPORTS = [
     "ifci_kernel_launches", "ifci_string_counts", "ifci_build_strings", "ifci_sigma", "ifci_hdiag",
     "ifci_frozen_core", "ifci_davidson_default_opts", "ifci_davidson_batched", "ifci_num_subsets",
     "ifci_increments", "ifci_rdm_backward", "ifci_profile_enable", "ifci_profile_read",
-    "ifci_sigma_noalloc", "ifci_sigma_noalloc_max_bytes", "ifci_h_elements",
+    "ifci_sigma_noalloc", "ifci_sigma_noalloc_max_bytes", "ifci_h_elements", "ifci_wait_selftest",
 ]
 PROFILE_KINDS = {"gather": 0, "contract": 1, "scatter": 2, "vector": 3, "other": 4, "contract_hi": 5}
 
@@ -50,7 +50,8 @@ class Problem(ctypes.Structure):
 
 class DavidsonOpts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("max_iter", c_int), ("max_space", c_int), ("e_tol", c_double),
-                ("r_tol", c_double), ("refine", c_int), ("hi_precision", c_int), ("det_budget", c_ll)]
+                ("r_tol", c_double), ("refine", c_int), ("hi_precision", c_int), ("det_budget", c_ll),
+                ("graph_iters", c_int)]
 
 
 def lib_path() -> str:
@@ -80,6 +81,7 @@ def load(build_if_missing: bool = True):
     L.ifci_build_strings.argtypes = [H, c_int, c_int, c_void_p, c_void_p, c_void_p]
     L.ifci_sigma.argtypes = [H, ctypes.POINTER(Strings), c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p]
     L.ifci_hdiag.argtypes = [H, ctypes.POINTER(Strings), c_void_p, c_void_p, c_void_p, c_void_p]
+    L.ifci_wait_selftest.argtypes = [H, ctypes.c_longlong, c_void_p]
     L.ifci_h_elements.argtypes = [H, ctypes.POINTER(Strings), c_void_p, c_void_p, ctypes.c_longlong, c_void_p,
                                   c_void_p, c_void_p, c_void_p]
     L.ifci_frozen_core.argtypes = [H, ctypes.POINTER(System), c_int, c_int_p, c_void_p, c_void_p, c_double_p,

@@ -163,6 +163,12 @@ def ifci_sigma_noalloc_max_bytes() -> int:
     return int(_lib().ifci_sigma_noalloc_max_bytes())
 
 
+def ifci_wait_selftest(handle: Handle, limit_cycles: int, stream=None) -> int:
+    """Runs out one bounded device wait on purpose; returns the C status
+    (IFCI_ERR_TIMEOUT expected)."""
+    return int(_lib().ifci_wait_selftest(handle.ptr, int(limit_cycles), _stream(stream)))
+
+
 def ifci_h_elements(handle: Handle, tables: StringTables, h1: torch.Tensor, eri: torch.Tensor,
                     bra: torch.Tensor, ket: torch.Tensor, stream=None) -> torch.Tensor:
     """<I|H|J> for int64 determinant index pairs (device tensors)."""

@@ -139,6 +139,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
     b.precision = o.precision;
     b.hi_precision = hi_prec;
     b.max_iter = o.max_iter;
+    b.graph_iters = o.graph_iters > 0 ? o.graph_iters : 0;
     b.e_tol = o.e_tol;
     b.r_tol = o.r_tol;
     SigmaPlan hi, lop;
@@ -280,6 +281,7 @@ void ifci_davidson_default_opts(ifci_davidson_opts_t *o) {
     o->refine = 1;
     o->hi_precision = IFCI_FP64E;
     o->det_budget = 0;
+    o->graph_iters = 0;
 }
 
 int ifci_davidson_batched(ifci_handle_t h, int nprob, const ifci_problem_t *probs, const ifci_davidson_opts_t *opts,

@@ -701,56 +701,126 @@ int dav_init(ifci_handle_t h, DavBatch &b, const HdiagDesc *d_hd, cudaStream_t s
     return IFCI_OK;
 }
 
-int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_plan, int *d_hi, int *d_lo,
-                void *D, void *G, int *h_nactive, cudaStream_t s) {
+// One Davidson iteration over the whole batch (no host synchronisation).
+static int dav_step(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_plan, int *d_hi, int *d_lo,
+                    void *D, void *G, cudaStream_t s) {
     const int nitem = (int)b.vitems.size();
     const bool mixed = lo_plan != nullptr;
     const int restart_at = b.max_space;
-    for (int it = 0; it < b.max_iter + 2; it++) {
-        select_kernel<<<(b.nprob + 127) / 128, 128, 0, s>>>(b.d_state, b.nprob, mixed ? 1 : 0, d_hi, d_lo);
+    select_kernel<<<(b.nprob + 127) / 128, 128, 0, s>>>(b.d_state, b.nprob, mixed ? 1 : 0, d_hi, d_lo);
+    IFCI_LAUNCH_CHECK(h);
+    IFCI_TRY(run_sigma(h, hi_plan, b.hi_precision, D, G, s));
+    if (mixed) IFCI_TRY(run_sigma(h, *lo_plan, b.precision, D, G, s));
+    ProfScope vec_scope(h, s, PK_VECTOR);
+    dots_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);
+    IFCI_LAUNCH_CHECK(h);
+    solve_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_gs, b.d_y);
+    IFCI_LAUNCH_CHECK(h);
+    residual_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, b.d_part);
+    IFCI_LAUNCH_CHECK(h);
+    IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_nactive, 0, sizeof(int), s));
+    // check_kernel records the subspace size before a restart (kold) for restart_kernel
+    check_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_coef, b.d_y, b.d_gs, b.max_space,
+                                        restart_at, b.keep, mixed ? 1 : 0, b.max_iter, b.e_tol, b.r_tol,
+                                        b.d_nactive);
+    IFCI_LAUNCH_CHECK(h);
+    restart_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, mixed ? 1 : 0);
+    IFCI_LAUNCH_CHECK(h);
+    for (int pass = 0; pass < 2; pass++) {
+        ortho_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_coef, b.max_space, b.d_part, pass);
         IFCI_LAUNCH_CHECK(h);
-        IFCI_TRY(run_sigma(h, hi_plan, b.hi_precision, D, G, s));
-        if (mixed) IFCI_TRY(run_sigma(h, *lo_plan, b.precision, D, G, s));
-        ProfScope vec_scope(h, s, PK_VECTOR);
-        dots_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);
+        reduce_coef_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_coef, pass);
         IFCI_LAUNCH_CHECK(h);
-        solve_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_gs, b.d_y);
-        IFCI_LAUNCH_CHECK(h);
-        residual_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, b.d_part);
-        IFCI_LAUNCH_CHECK(h);
-        IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_nactive, 0, sizeof(int), s));
-        // check_kernel records the subspace size before a restart (kold) for restart_kernel
-        check_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_coef, b.d_y, b.d_gs, b.max_space,
-                                            restart_at, b.keep, mixed ? 1 : 0, b.max_iter, b.e_tol, b.r_tol,
-                                            b.d_nactive);
-        IFCI_LAUNCH_CHECK(h);
-        restart_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, mixed ? 1 : 0);
-        IFCI_LAUNCH_CHECK(h);
-        for (int pass = 0; pass < 2; pass++) {
-            ortho_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_coef, b.max_space, b.d_part,
-                                               pass);
-            IFCI_LAUNCH_CHECK(h);
-            reduce_coef_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_coef, pass);
-            IFCI_LAUNCH_CHECK(h);
+    }
+    normalize_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.max_space);
+    IFCI_LAUNCH_CHECK(h);
+    advance_kernel<<<(b.nprob + 127) / 128, 128, 0, s>>>(b.d_probs, b.d_state, b.nprob, b.r_tol, mixed ? 1 : 0);
+    IFCI_LAUNCH_CHECK(h);
+    if (h->prof) prof_end(h, s);
+    return IFCI_OK;
+}
+
+// Iterates until every problem has stopped.  Eager mode launches each
+// iteration and reads the active count after it; graph mode (b.graph_iters > 0,
+// profiling off) runs the first iteration eagerly (it also configures the
+// kernels), then captures b.graph_iters iterations into one CUDA graph on a
+// stream of its own (ordered after `s` by an event) and replays it, reading
+// the active count after each replay.  Problems that stop inside a block make
+// the remaining iterations of the block no-ops, so both modes give the same
+// results.
+int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_plan, int *d_hi, int *d_lo,
+                void *D, void *G, int *h_nactive, cudaStream_t s) {
+    const int nitem = (int)b.vitems.size();
+    const bool graph = b.graph_iters > 0 && !h->prof;
+    cudaStream_t ws = s;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraph_t gr = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long launches_per_graph = 0;
+    int st = IFCI_OK;
+    if (graph) {
+        IFCI_CUDA_TRY(h, cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
+        IFCI_CUDA_TRY(h, cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+        IFCI_CUDA_TRY(h, cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+        IFCI_CUDA_TRY(h, cudaEventRecord(ev_in, s));
+        IFCI_CUDA_TRY(h, cudaStreamWaitEvent(ws, ev_in, 0));
+    }
+    for (int it = 0; it < b.max_iter + 2 && st == IFCI_OK;) {
+        if (graph && it > 0) {
+            if (!exec) {
+                const long long l0 = h->launches;
+                if (cudaStreamBeginCapture(ws, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                    st = set_error(h, IFCI_ERR_CUDA, "davidson: stream capture could not begin");
+                    break;
+                }
+                for (int g = 0; g < b.graph_iters && st == IFCI_OK; g++)
+                    st = dav_step(h, b, hi_plan, lo_plan, d_hi, d_lo, D, G, ws);
+                const cudaError_t ec = cudaStreamEndCapture(ws, &gr);
+                if (st != IFCI_OK) break;
+                if (ec != cudaSuccess || cudaGraphInstantiate(&exec, gr, 0) != cudaSuccess) {
+                    cudaGetLastError();
+                    st = set_error(h, IFCI_ERR_CUDA, "davidson: graph capture failed");
+                    break;
+                }
+                launches_per_graph = h->launches - l0;
+                h->launches = l0;   // counted when replayed
+            }
+            if (cudaGraphLaunch(exec, ws) != cudaSuccess) {
+                st = set_error(h, IFCI_ERR_CUDA, "davidson: graph launch failed");
+                break;
+            }
+            h->launches += launches_per_graph;
+            it += b.graph_iters;
+        } else {
+            st = dav_step(h, b, hi_plan, lo_plan, d_hi, d_lo, D, G, ws);
+            if (st != IFCI_OK) break;
+            it += 1;
         }
-        normalize_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.max_space);
-        IFCI_LAUNCH_CHECK(h);
-        advance_kernel<<<(b.nprob + 127) / 128, 128, 0, s>>>(b.d_probs, b.d_state, b.nprob, b.r_tol,
-                                                             mixed ? 1 : 0);
-        IFCI_LAUNCH_CHECK(h);
-        if (h->prof) prof_end(h, s);
-        IFCI_CUDA_TRY(h, cudaMemcpyAsync(h_nactive, b.d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
-        IFCI_CUDA_TRY(h, cudaMemcpyAsync(h_nactive + 1, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-        IFCI_CUDA_TRY(h, cudaStreamSynchronize(s));
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(h_nactive, b.d_nactive, sizeof(int), cudaMemcpyDeviceToHost, ws));
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(h_nactive + 1, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, ws));
+        IFCI_CUDA_TRY(h, cudaStreamSynchronize(ws));
         if (h_nactive[1]) {
-            cudaMemsetAsync(h->d_err, 0, sizeof(int), s);
-            return set_error(h, IFCI_ERR_TIMEOUT, "davidson: a bounded device wait ran out");
+            cudaMemsetAsync(h->d_err, 0, sizeof(int), ws);
+            st = set_error(h, IFCI_ERR_TIMEOUT, "davidson: a bounded device wait ran out");
+            break;
         }
         if (*h_nactive == 0) break;
     }
-    ritz_out_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y);
-    IFCI_LAUNCH_CHECK(h);
-    return IFCI_OK;
+    if (st == IFCI_OK) {
+        ritz_out_kernel<<<nitem, 256, 0, ws>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y);
+        IFCI_LAUNCH_CHECK(h);
+    }
+    if (graph) {
+        cudaEventRecord(ev_out, ws);
+        cudaStreamWaitEvent(s, ev_out, 0);
+        cudaStreamSynchronize(ws);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (gr) cudaGraphDestroy(gr);
+        cudaEventDestroy(ev_in);
+        cudaEventDestroy(ev_out);
+        cudaStreamDestroy(ws);
+    }
+    return st;
 }
 
 }  // namespace ifci

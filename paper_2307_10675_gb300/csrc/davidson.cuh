@@ -75,6 +75,7 @@ __host__ __device__ inline void start_block(int nstr, int max_space, int *nv, in
 struct DavBatch {
     int nprob = 0, max_space = 12;
     int keep = kKeep;             // Ritz vectors kept at a thick restart (<= max_space - 2)
+    int graph_iters = 0;          // iterations per captured CUDA graph (0: eager launches)
     int precision = IFCI_FP64;
     int hi_precision = IFCI_FP64;
     int max_iter = 100;
