@@ -484,7 +484,7 @@ def c4_case(args, torch, ifci):
     res = {}
     with ifci.Handle(0, 0) as h:
         for name, prec, hi in paths:
-            opts = ifci.davidson_opts(prec, hi_precision=hi, r_tol=1e-6, e_tol=1e-10, max_iter=300)
+            opts = ifci.davidson_opts(prec, hi_precision=hi, r_tol=1e-7, e_tol=1e-11, max_iter=300)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             out = ifci.ifci_increments(h, sysd, 3, opts)
