@@ -72,20 +72,6 @@ inline long long row_tile_count(int nstr) {
     return (nstr + rmax - 1) / rmax;
 }
 
-// amap[r][A] = index of pair A in the alpha list of row ka0 + r, or -1.
-// Called by all threads of the CTA; ends with __syncthreads().
-__device__ __forceinline__ void build_alpha_map(int16_t *amap, int np_pad, const SigmaProb &p, const TileGeom &g) {
-    const int nexc = p.nexc;
-    for (int i = threadIdx.x; i < g.R * np_pad; i += blockDim.x) amap[i] = -1;
-    __syncthreads();
-    for (int i = threadIdx.x; i < g.R * nexc; i += blockDim.x) {
-        const int r = i / nexc, e = i % nexc;
-        const int32_t x = p.exc[(size_t)(g.ka0 + r) * nexc + e];
-        amap[r * np_pad + exc_pair(x)] = (int16_t)e;
-    }
-    __syncthreads();
-}
-
 }  // namespace tcg
 }  // namespace ifci
 

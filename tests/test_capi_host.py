@@ -63,3 +63,44 @@ def test_handle_create_without_gpu_fails_cleanly():
     from paper_2307_10675_gb300 import Handle, IfciError
     with pytest.raises(IfciError):
         Handle(0, 0)
+
+
+def _header_struct_fields(name):
+    src = open(os.path.join(ROOT, "include", "ifci.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    m = re.search(r"typedef struct\s*\{([^{}]*)\}\s*" + name + r"\s*;", src)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        parts = [p.strip() for p in decl.split(",") if p.strip()]
+        if not parts:
+            continue
+        fields.append(parts[0].split()[-1].lstrip("*").split("[")[0])
+        fields += [p.lstrip("*").split("[")[0].strip() for p in parts[1:]]
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("ifci_davidson_opts_t", "DavidsonOpts"), ("ifci_problem_t", "Problem"),
+                                           ("ifci_system_t", "System"), ("ifci_strings_t", "Strings")])
+def test_binding_structs_follow_the_header(cname, pyname):
+    """The ctypes mirrors list the header's fields in the header's order."""
+    from paper_2307_10675_gb300 import _capi
+    fields = [f[0] for f in getattr(_capi, pyname)._fields_]
+    assert fields == _header_struct_fields(cname)
+
+
+def test_davidson_default_opts_from_the_library():
+    from paper_2307_10675_gb300 import _capi
+    o = _capi.DavidsonOpts()
+    _capi.load().ifci_davidson_default_opts(ctypes.byref(o))
+    assert (o.precision, o.max_iter, o.max_space) == (_capi.IFCI_FP64, 100, 12)
+    assert (o.e_tol, o.r_tol) == (1e-10, 1e-6)
+    assert o.hi_precision == _capi.IFCI_FP64E
+    assert o.det_budget == 0 and o.graph_iters == 0
+
+
+def test_sigma_flag_matches_the_header():
+    from paper_2307_10675_gb300 import _capi
+    src = open(os.path.join(ROOT, "include", "ifci.h")).read()
+    m = re.search(r"#define\s+IFCI_SIGMA_SPIN_SYMMETRIC\s+(0x[0-9a-fA-F]+|\d+)", src)
+    assert m and int(m.group(1), 0) == _capi.IFCI_SIGMA_SPIN_SYMMETRIC
