@@ -115,6 +115,22 @@ inline size_t ws_round(size_t bytes) { return (bytes + 255) & ~size_t(255); }
 inline cudaStream_t as_cuda(ifci_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
 
 int device_sm_count(int device);
+
+// The dynamic shared memory a kernel may use is a per-device attribute: each
+// caller keeps one of these per kernel and raises the attribute on a device
+// the first time that device needs more than it was opened up to.
+constexpr int kMaxDevices = 64;
+struct SmemOptIn {
+    int bytes[kMaxDevices] = {};
+};
+template <typename K>
+inline cudaError_t ensure_smem(SmemOptIn &opt, int device, K kernel, int bytes) {
+    if (device < 0 || device >= kMaxDevices) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (bytes <= opt.bytes[device]) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) opt.bytes[device] = bytes;
+    return e;
+}
 int launch_exc_blocks(ifci_handle_t h, int nstr, int nexc, const int32_t *exc, uint8_t *blk, cudaStream_t s);
 // row stride (int32 entries) of the dense pair map
 __host__ __device__ inline int pmap_ld(int np) { return (np + 15) / 16 * 16; }

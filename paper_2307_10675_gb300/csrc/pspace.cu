@@ -396,11 +396,8 @@ int launch_pspace_start(ifci_handle_t h, const DavBatch &b, const HdiagDesc *d_h
     psp_select_kernel<<<b.nprob, kSelThreads, 0, s>>>(b.d_probs, pidx, pcount);
     IFCI_LAUNCH_CHECK(h);
     const int smem = 2 * kPsp * kPsp * (int)sizeof(double);   // 64 KB
-    static bool configured = false;
-    if (!configured) {
-        IFCI_CUDA_TRY(h, cudaFuncSetAttribute(psp_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        configured = true;
-    }
+    static SmemOptIn opt;
+    IFCI_CUDA_TRY(h, ensure_smem(opt, h->device, psp_solve_kernel, smem));
     psp_solve_kernel<<<b.nprob, kPsp, smem, s>>>(b.d_probs, d_hd, pidx, pcount, b.d_state, b.max_space);
     IFCI_LAUNCH_CHECK(h);
     norm_part_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);

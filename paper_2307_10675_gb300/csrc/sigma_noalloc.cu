@@ -14,7 +14,6 @@ namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB on every device that loads the library
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
-constexpr int kMaxDevices = 64;
 void *g_scratch_addr[kMaxDevices];  // device address of g_static_scratch, per device
 
 // Work lists of the single problem: gather/scatter items and 64 x 64 contraction tiles.

@@ -371,12 +371,8 @@ int launch_oz_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &
             return set_error(h, IFCI_ERR_UNSUPPORTED, "FP64E: npair %d > %d (exact level sums)", p.np, kMaxNpExact);
     if (!h->d_err || !h->d_counter) return set_error(h, IFCI_ERR_INVALID_ARG, "FP64E: no error flag / counter");
     const size_t smem = 1024 + 2 * kWStage + kAStage;   // 205,824 B
-    static bool configured = false;
-    if (!configured) {
-        IFCI_CUDA_TRY(h, cudaFuncSetAttribute(oz_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem));
-        configured = true;
-    }
+    static SmemOptIn opt;
+    IFCI_CUDA_TRY(h, ensure_smem(opt, h->device, oz_contract_kernel, (int)smem));
     const int grid = std::min(w.ntc, device_sm_count(h->device));
     IFCI_CUDA_TRY(h, cudaMemsetAsync(h->d_counter, 0, sizeof(int), s));
     ProfScope ps(h, s, PK_CONTRACT_HI);

@@ -205,12 +205,8 @@ int launch_tc_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &
     const size_t smem = std::max(tc_smem_bytes(max_np), (size_t)116 * 1024);
     const size_t wmax = (size_t)k_atoms(max_np) * n_pad(max_np) * kAtomBytes;
     const size_t amax = (size_t)k_atoms(max_np) * kTM * kAtomBytes;
-    static int configured_smem = 0;
-    if ((int)smem > configured_smem) {
-        IFCI_CUDA_TRY(h, cudaFuncSetAttribute(tc_contract_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem));
-        configured_smem = (int)smem;
-    }
+    static SmemOptIn opt;
+    IFCI_CUDA_TRY(h, ensure_smem(opt, h->device, tc_contract_bf16_kernel, (int)smem));
     if (!h->d_counter) return set_error(h, IFCI_ERR_INVALID_ARG, "tensor-core path: no tile counter");
     const int grid = std::min(w.ntc, device_sm_count(h->device));
     IFCI_CUDA_TRY(h, cudaMemsetAsync(h->d_counter, 0, sizeof(int), s));
