@@ -232,10 +232,12 @@ typedef struct {
     int max_space;       /* subspace size before a restart, 3..24 (default 12) */
     double e_tol;        /* convergence: |E_k - E_{k-1}| < e_tol (default 1e-10 Eh) */
     double r_tol;        /* and ||H x - E x||_2 < r_tol (default 1e-6) */
-    int refine;          /* non-FP64 precision: finish with FP64 sigma refinement (default 1) */
+    int refine;          /* >= 0: ifci_increments keeps the converged vectors in the handle
+                            for ifci_rdm_backward; < 0: it does not (default 1).  Mixed
+                            precision always finishes on exact sigmas. */
     int hi_precision;    /* mixed mode: sigma of restart vectors, IFCI_FP64 or IFCI_FP64E
                             (default IFCI_FP64E) */
-    long long det_budget;/* determinants per sigma wave (0 = from workspace size) */
+    long long det_budget;/* D elements (npair x determinants) per sigma wave; 0 = 2^31 */
     int graph_iters;     /* > 0: Davidson iterations are captured in blocks of this
                             many into one CUDA graph, replayed on a stream of the
                             handle (event-ordered with `stream`); 0 = launched one
@@ -248,7 +250,18 @@ void ifci_davidson_default_opts(ifci_davidson_opts_t *opts);
 
 /* ifci_davidson_batched — lowest singlet eigenpair of each problem's
  * H + e_core (Davidson in the spin-flip-even sector c = c^T, which holds
- * S = 0, 2, ...; diagonal preconditioner; classical Gram-Schmidt done twice).
+ * S = 0, 2, ...; diagonal preconditioner; classical Gram-Schmidt with a
+ * second pass when the first removes more than half of the correction).
+ * Start: the lowest eigenvectors of H among the 64 lowest-diagonal pair
+ * functions (one per decoupled block of that small matrix first) plus a
+ * random vector orthogonal to them; thick restarts keep the four lowest Ritz
+ * vectors; Ritz roots within 0.3 Eh of the lowest are corrected in turn
+ * until resolved.  When H splits into (nearly) decoupled sectors (charge
+ * distributions over distant bodies) the lowest sector is found by these
+ * heuristics, not by construction.  Mixed precision (precision = BF16/FP32)
+ * runs a low-precision phase, then rebuilds exact sigmas (hi_precision) of
+ * its kept Ritz vectors and finishes exactly; convergence is only judged on
+ * exact sigmas.
  *   energies : host double[nprob], eigenvalues including e_core.
  *   iters    : host int[nprob] or NULL, sigma builds per problem.
  *   status   : host int[nprob] or NULL, IFCI_OK or IFCI_ERR_NOT_CONVERGED.
