@@ -243,6 +243,11 @@ typedef struct {
                             handle (event-ordered with `stream`); 0 = launched one
                             by one (default).  Ignored while profiling is on.
                             Results are identical either way. */
+    int sector_passes;   /* 2: problems whose start matrix (the P-space of the lowest
+                            -diagonal pair functions) splits into decoupled blocks with a
+                            second block within 0.3 Eh of the lowest are solved again
+                            from that block's lowest vector, and the lower result (energy
+                            and vector) is kept; 0 or 1: one pass (default 0). */
 } ifci_davidson_opts_t;
 
 /* Fills opts with the defaults listed above (precision IFCI_FP64). */

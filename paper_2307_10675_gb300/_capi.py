@@ -51,7 +51,7 @@ class Problem(ctypes.Structure):
 class DavidsonOpts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("max_iter", c_int), ("max_space", c_int), ("e_tol", c_double),
                 ("r_tol", c_double), ("refine", c_int), ("hi_precision", c_int), ("det_budget", c_ll),
-                ("graph_iters", c_int)]
+                ("graph_iters", c_int), ("sector_passes", c_int)]
 
 
 def lib_path() -> str:

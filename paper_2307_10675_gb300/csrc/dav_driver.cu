@@ -54,7 +54,8 @@ static void dav_layout(const std::vector<ProbSpec> &specs, const ifci_davidson_o
     z.bytes += ws_round(n * sizeof(DavProb)) + ws_round(n * sizeof(DavState)) + ws_round(z.nitem * sizeof(WorkItem));
     z.bytes += ws_round((size_t)z.nitem * kNP * 8) + ws_round(n * kMaxSpace * kMaxSpace * 8) +
                ws_round(n * kYStride * 8) + ws_round(n * kNP * 8) + ws_round(8) + 2 * ws_round(n * 4);
-    z.bytes += ws_round(n * sizeof(FoldDesc)) + ws_round(n * sizeof(HdiagDesc)) + psp_workspace_bytes((int)n);
+    z.bytes += ws_round(n * sizeof(FoldDesc)) + ws_round(n * sizeof(HdiagDesc)) + psp_workspace_bytes((int)n) +
+               ws_round(n * 2 * sizeof(double));
     z.bytes += ws_round((size_t)z.nitem * sizeof(int)) + ws_round((size_t)z.nitem * sizeof(long long));
     // two sigma plans (hi and lo)
     z.bytes += 2 * (ws_round(n * sizeof(SigmaProb)) + ws_round((size_t)z.n_items_sigma * sizeof(WorkItem)) +
@@ -89,7 +90,7 @@ int check_opts(ifci_handle_t h, const ifci_davidson_opts_t &o) {
 }
 
 int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o, double *energies,
-              int *iters, int *status, cudaStream_t s) {
+              int *iters, int *status, cudaStream_t s, double *blk_energy) {
     const int n = (int)specs.size();
     if (n == 0) return IFCI_OK;
     IFCI_TRY(check_opts(h, o));
@@ -179,6 +180,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
         dp.hd = hd;
         dp.c_out = p.c_out;
         dp.e_core = p.e_core;
+        dp.seed_block = p.seed_block;
         b.probs.push_back(dp);
         SigmaProb sp{};
         sp.n = p.n; sp.nstr = nstr; sp.nexc = nexc; sp.np = np; sp.ld = np;
@@ -202,6 +204,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
     b.d_y = ws_take<double>(h, (size_t)n * kYStride);
     b.d_coef = ws_take<double>(h, (size_t)n * kNP);
     b.d_nactive = ws_take<int>(h, 2);
+    b.d_blk_energy = ws_take<double>(h, (size_t)n * 2);
     int *d_hi = ws_take<int>(h, n), *d_lo = ws_take<int>(h, n);
     auto *d_fold = ws_take<FoldDesc>(h, n);
     auto *d_hd = ws_take<HdiagDesc>(h, n);
@@ -255,6 +258,9 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
     IFCI_TRY(st);
     std::vector<DavState> hs(n);
     IFCI_CUDA_TRY(h, cudaMemcpyAsync(hs.data(), b.d_state, n * sizeof(DavState), cudaMemcpyDeviceToHost, s));
+    if (blk_energy)
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(blk_energy, b.d_blk_energy, (size_t)n * 2 * sizeof(double),
+                                         cudaMemcpyDeviceToHost, s));
     IFCI_CUDA_TRY(h, cudaStreamSynchronize(s));
     int ret = IFCI_OK;
     for (int i = 0; i < n; i++) {
@@ -264,6 +270,72 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
         if (hs[i].status != IFCI_OK) ret = IFCI_ERR_NOT_CONVERGED;
     }
     if (ret != IFCI_OK) set_error(h, ret, "davidson: some problems did not converge");
+    return ret;
+}
+
+int dav_solve_sectors(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o,
+                      double *energies, int *iters, int *status, cudaStream_t s) {
+    const int n = (int)specs.size();
+    if (o.sector_passes < 2 || n == 0) return dav_solve(h, specs, o, energies, iters, status, s);
+    const size_t mark = h->ws_top;
+    std::vector<int> st_local;
+    if (!status) {   // the merge needs every problem's status
+        st_local.assign(n, IFCI_OK);
+        status = st_local.data();
+    }
+    std::vector<double> blk((size_t)n * 2, 1e300);
+    const int r1 = dav_solve(h, specs, o, energies, iters, status, s, blk.data());
+    if (r1 != IFCI_OK && r1 != IFCI_ERR_NOT_CONVERGED) return r1;
+    // second pass: problems with a competitive second block, seeded from it
+    std::vector<ProbSpec> again;
+    std::vector<int> who;
+    std::vector<size_t> voff;
+    size_t vbytes = 0;
+    for (int i = 0; i < n; i++) {
+        if (!(blk[2 * i + 1] < 1e299 && blk[2 * i + 1] <= blk[2 * i] + kSectorWindow)) continue;
+        ProbSpec q = specs[i];
+        q.seed_block = 1;
+        voff.push_back(vbytes);
+        if (q.c_out) vbytes += (size_t)binom(q.n, q.m) * binom(q.n, q.m) * sizeof(double);
+        again.push_back(q);
+        who.push_back(i);
+    }
+    if (again.empty()) return r1;
+    double *tmp = nullptr;
+    if (vbytes) IFCI_CUDA_TRY(h, cudaMalloc(&tmp, vbytes));
+    for (size_t k = 0; k < again.size(); k++)
+        if (again[k].c_out) again[k].c_out = reinterpret_cast<double *>(reinterpret_cast<char *>(tmp) + voff[k]);
+    std::vector<double> e2(again.size());
+    std::vector<int> it2(again.size()), st2(again.size());
+    h->ws_top = mark;
+    const int r2 = dav_solve(h, again, o, e2.data(), it2.data(), st2.data(), s);
+    int ret = IFCI_OK;
+    if (r2 == IFCI_OK || r2 == IFCI_ERR_NOT_CONVERGED) {
+        for (size_t k = 0; k < again.size(); k++) {
+            const int i = who[k];
+            if (iters) iters[i] += it2[k];
+            if (st2[k] == IFCI_OK && (status[i] != IFCI_OK || e2[k] < energies[i])) {
+                energies[i] = e2[k];
+                status[i] = IFCI_OK;
+                if (specs[i].c_out) {
+                    const size_t bytes = (size_t)binom(again[k].n, again[k].m) * binom(again[k].n, again[k].m) * 8;
+                    if (cudaMemcpyAsync(specs[i].c_out, again[k].c_out, bytes, cudaMemcpyDeviceToDevice, s) !=
+                        cudaSuccess)
+                        ret = set_error(h, IFCI_ERR_CUDA, "davidson: copy of a second-pass vector");
+                }
+            }
+        }
+        if (ret == IFCI_OK)
+            for (int i = 0; i < n; i++)
+                if (status[i] != IFCI_OK) ret = IFCI_ERR_NOT_CONVERGED;
+    } else {
+        ret = r2;
+    }
+    if (tmp) {
+        cudaStreamSynchronize(s);
+        cudaFree(tmp);
+    }
+    if (ret == IFCI_ERR_NOT_CONVERGED) set_error(h, ret, "davidson: some problems did not converge");
     return ret;
 }
 
@@ -282,6 +354,7 @@ void ifci_davidson_default_opts(ifci_davidson_opts_t *o) {
     o->hi_precision = IFCI_FP64E;
     o->det_budget = 0;
     o->graph_iters = 0;
+    o->sector_passes = 0;
 }
 
 int ifci_davidson_batched(ifci_handle_t h, int nprob, const ifci_problem_t *probs, const ifci_davidson_opts_t *opts,
@@ -303,7 +376,7 @@ int ifci_davidson_batched(ifci_handle_t h, int nprob, const ifci_problem_t *prob
     IFCI_TRY(check_opts(h, o));
     IFCI_CUDA_TRY(h, cudaSetDevice(h->device));
     IFCI_TRY(ws_reserve(h, dav_workspace_bytes(specs, o)));
-    return dav_solve(h, specs, o, energies, iters, status, as_cuda(stream));
+    return dav_solve_sectors(h, specs, o, energies, iters, status, as_cuda(stream));
 }
 
 }  // extern "C"

@@ -11,6 +11,8 @@ struct ProbSpec {
     const double *eri;      // device npair*npair
     double e_core;
     double *c_out;          // device nstr*nstr or nullptr
+    int seed_block = 0;     // 0: the default start block; r >= 1: start from the lowest vector of the
+                            // r-th lowest decoupled block of the P-space matrix
 };
 
 struct DavSizes {
@@ -28,7 +30,12 @@ size_t dav_workspace_bytes(const std::vector<ProbSpec> &specs, const ifci_davids
 // whatever the caller already took.  Outputs are host arrays (may be null
 // except energies).  Synchronous.
 int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o, double *energies,
-              int *iters, int *status, cudaStream_t s);
+              int *iters, int *status, cudaStream_t s, double *blk_energy = nullptr);
+// dav_solve, then (opts.sector_passes >= 2) a second pass over the problems
+// whose P-space shows a competitive second block; the workspace above `mark`
+// is reused by the second pass.
+int dav_solve_sectors(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o,
+                      double *energies, int *iters, int *status, cudaStream_t s);
 int dav_init(ifci_handle_t h, DavBatch &b, const HdiagDesc *d_hd, cudaStream_t s);
 size_t psp_workspace_bytes(int nprob);
 int launch_pspace_start(ifci_handle_t h, const DavBatch &b, const HdiagDesc *d_hd, cudaStream_t s);

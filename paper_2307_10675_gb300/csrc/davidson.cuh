@@ -8,7 +8,7 @@ struct DavProb {
     long long ndet;
     int nstr;
     int item0, nitem;        // range of vector work items
-    int pad_;
+    int seed_block;          // 0: default start block; r >= 1: from the r-th P-space block (second pass)
     double *B;               // (max_space + 1) slots of ndet: basis vectors
     double *S;               // (max_space + 1) slots of ndet: sigma of each slot
     const double *hd;        // diagonal <I|H|I> (no constant)
@@ -59,6 +59,7 @@ constexpr int kYStride = kKeep * kNP;
 // vector that vanishes on the P-space determinants (exactly orthogonal to them)
 constexpr int kStartP = 3;
 constexpr int kPspMax = 64;
+constexpr double kSectorWindow = 0.3;   // a second P-space block this close (Eh) gets its own pass
 
 // start block layout of a problem with nstr strings and subspace max_space
 __host__ __device__ inline void start_block(int nstr, int max_space, int *nv, int *noise_slot) {
@@ -76,6 +77,7 @@ struct DavBatch {
     int nprob = 0, max_space = 12;
     int keep = kKeep;             // Ritz vectors kept at a thick restart (<= max_space - 2)
     int graph_iters = 0;          // iterations per captured CUDA graph (0: eager launches)
+    double *d_blk_energy = nullptr;   // [nprob][2] lowest eigenvalue of the two lowest P-space blocks
     int precision = IFCI_FP64;
     int hi_precision = IFCI_FP64;
     int max_iter = 100;

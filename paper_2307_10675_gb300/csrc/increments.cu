@@ -190,7 +190,7 @@ int ifci_increments(ifci_handle_t h, const ifci_system_t *sys, int max_order, co
             sp.push_back(ProbSpec{P.nA[x], (int)P.subsets[x].size(), d_h1 + h1_off[x], d_eri + eri_off[x], ecore[x],
                                   keep ? h->kept.vec + vec_off[x] : nullptr});
         h->ws_top = mark;
-        int r = dav_solve(h, sp, o, ex.data() + bt.first, its.data() + bt.first, st.data() + bt.first, s);
+        int r = dav_solve_sectors(h, sp, o, ex.data() + bt.first, its.data() + bt.first, st.data() + bt.first, s);
         if (r != IFCI_OK && r != IFCI_ERR_NOT_CONVERGED) return r;
         if (r != IFCI_OK) ret = r;
     }

@@ -179,7 +179,8 @@ psp_select_kernel(const DavProb *__restrict__ probs, long long *__restrict__ pid
 // slots 0..nv-1; the random start vector is cleared on the P-space determinants.
 __global__ void __launch_bounds__(kPsp)
 psp_solve_kernel(const DavProb *__restrict__ probs, const HdiagDesc *__restrict__ hdd, const long long *__restrict__ pidx,
-                 const int *__restrict__ pcount, const DavState *__restrict__ st, int max_space) {
+                 const int *__restrict__ pcount, const DavState *__restrict__ st, int max_space,
+                 double *__restrict__ blk_energy) {
     extern __shared__ double psm[];
     double *A = psm;                       // [kPsp][kPsp]
     double *V = psm + kPsp * kPsp;         // [kPsp][kPsp]
@@ -300,22 +301,50 @@ psp_solve_kernel(const DavProb *__restrict__ probs, const HdiagDesc *__restrict_
                 if (fabs(V[i * kPsp + b]) > fabs(V[g * kPsp + b])) g = i;
             blk[r] = comp[g];
         }
-        // first the lowest eigenvector of each block (in order of those
-        // eigenvalues), then the next lowest eigenvectors
+        // rank of each block by its lowest eigenvalue: first[] = the eigenpair
+        // index (in ascending order) that opens block rank 0, 1, ...
+        int first[kPsp], nb = 0;
+        for (int r = 0; r < P; r++) {
+            bool opens = true;
+            for (int q = 0; q < r; q++)
+                if (blk[q] == blk[r]) opens = false;
+            if (opens) first[nb++] = r;
+        }
+        if (blk_energy) {
+            blk_energy[2 * blockIdx.x] = A[order[first[0]] * kPsp + order[first[0]]];
+            blk_energy[2 * blockIdx.x + 1] = nb > 1 ? A[order[first[1]] * kPsp + order[first[1]]] : 1e300;
+        }
         bool taken[kPsp];
         for (int r = 0; r < P; r++) taken[r] = false;
         int nc = 0;
-        for (int r = 0; r < P && nc < nv; r++) {
-            bool first = true;
-            for (int q = 0; q < r; q++)
-                if (blk[q] == blk[r]) first = false;
-            if (first) {
-                cols[nc++] = order[r];
-                taken[r] = true;
+        const int seed = p.seed_block;
+        if (seed > 0 && seed < nb) {
+            // second pass: that block's lowest vector first, then the lowest
+            // eigenvectors outside the blocks ranked below it
+            cols[nc++] = order[first[seed]];
+            taken[first[seed]] = true;
+            for (int r = 0; r < P && nc < nv; r++) {
+                bool lower = false;
+                for (int q = 0; q < seed; q++)
+                    if (blk[r] == blk[first[q]]) lower = true;
+                if (!taken[r] && !lower) {
+                    cols[nc++] = order[r];
+                    taken[r] = true;
+                }
+            }
+        } else {
+            // first the lowest eigenvector of each block (in order of those
+            // eigenvalues), then the next lowest eigenvectors
+            for (int k = 0; k < nb && nc < nv; k++) {
+                cols[nc++] = order[first[k]];
+                taken[first[k]] = true;
             }
         }
         for (int r = 0; r < P && nc < nv; r++)
-            if (!taken[r]) cols[nc++] = order[r];
+            if (!taken[r]) {
+                cols[nc++] = order[r];
+                taken[r] = true;
+            }
     }
     __syncthreads();
     if (t < P) {
@@ -398,7 +427,8 @@ int launch_pspace_start(ifci_handle_t h, const DavBatch &b, const HdiagDesc *d_h
     const int smem = 2 * kPsp * kPsp * (int)sizeof(double);   // 64 KB
     static SmemOptIn opt;
     IFCI_CUDA_TRY(h, ensure_smem(opt, h->device, psp_solve_kernel, smem));
-    psp_solve_kernel<<<b.nprob, kPsp, smem, s>>>(b.d_probs, d_hd, pidx, pcount, b.d_state, b.max_space);
+    psp_solve_kernel<<<b.nprob, kPsp, smem, s>>>(b.d_probs, d_hd, pidx, pcount, b.d_state, b.max_space,
+                                                  b.d_blk_energy);
     IFCI_LAUNCH_CHECK(h);
     norm_part_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);
     IFCI_LAUNCH_CHECK(h);

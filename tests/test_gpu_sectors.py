@@ -1,0 +1,76 @@
+"""Second pass over decoupled sectors (sector_passes = 2, opt-in): every
+2-body set of the 40-body chain reaches the oracle's lowest eigenvalue in
+FP64E; in FP64 it rescues one of the five one-pass misses and not the other
+four (expected failure); the hard 3-body sets and their vectors are right;
+the option changes nothing where the P-space has no competitive second
+block."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from synth import chain_4x2, chain_40_uneven
+
+import paper_2307_10675_gb300 as ifci
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _system(chain):
+    return ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=DEV),
+                             torch.tensor(chain.eri_packed(), device=DEV))
+
+
+@pytest.mark.parametrize("prec,hi,tol", [
+    ("fp64e", "fp64e", 1e-8),
+    pytest.param("fp64", "fp64", 1e-8, marks=pytest.mark.xfail(
+        strict=False, reason="four sets stay in a higher state: their lower state is not a separate block of "
+                             "the 64-function P-space, so the second pass is not triggered for it"))])
+def test_two_pass_order2_every_set_against_oracle(prec, hi, tol):
+    chain = chain_40_uneven()
+    gold = json.load(open(os.path.join(GOLDEN, "chain40_pairs_oracle.json")))
+    with ifci.Handle(0, 0) as h:
+        o = ifci.ifci_increments(h, _system(chain), 2, ifci.davidson_opts(
+            prec, hi_precision=hi, r_tol=1e-7, e_tol=1e-11, max_iter=300, sector_passes=2))
+    assert np.all(o["status"] == 0)
+    bad = []
+    for i, X in enumerate(ifci.body_subsets(40, 2)):
+        if len(X) == 2:
+            ref = gold["energies"][",".join(map(str, X))]["energy"]
+            if abs(o["e_x"][i] - ref) > tol:
+                bad.append((X, o["e_x"][i] - ref))
+    assert not bad, bad
+
+
+def test_two_pass_hard_sets_and_vectors():
+    chain = chain_40_uneven()
+    gold = json.load(open(os.path.join(GOLDEN, "chain40_oracle.json")))
+    sets = [(8, 20, 32), (12, 20, 27), (17, 21, 34), (7, 20, 21), (8, 14, 39)]
+    with ifci.Handle(0, 0) as h:
+        sysa = _system(chain)
+        probs = []
+        for X in sets:
+            h1, eri, ec = ifci.ifci_frozen_core(h, sysa, X)
+            n = h1.shape[0]
+            import math
+            c = torch.empty(math.comb(n, 3) ** 2, dtype=torch.float64, device=DEV)
+            probs.append(ifci.CIProblem(n, len(X), h1, eri, ec, c_out=c))
+        e, it, st = ifci.ifci_davidson_batched(h, probs, ifci.davidson_opts(
+            "fp64e", r_tol=1e-7, e_tol=1e-11, max_iter=300, sector_passes=2))
+        torch.cuda.synchronize()
+    assert np.all(st == 0)
+    np.testing.assert_allclose(e, [gold["energies"][",".join(map(str, X))]["energy"] for X in sets], atol=1e-8)
+    for p in probs:   # the returned vector is the winning pass's normalised eigenvector
+        assert abs(float(torch.linalg.vector_norm(p.c_out)) - 1.0) < 1e-10
+
+
+def test_two_pass_is_a_no_op_without_competitive_blocks():
+    chain = chain_4x2()
+    with ifci.Handle(0, 0) as h:
+        a = ifci.ifci_increments(h, _system(chain), 2, ifci.davidson_opts("fp64e"))
+        b = ifci.ifci_increments(h, _system(chain), 2, ifci.davidson_opts("fp64e", sector_passes=2))
+    np.testing.assert_allclose(b["e_x"], a["e_x"], rtol=0, atol=1e-12)
