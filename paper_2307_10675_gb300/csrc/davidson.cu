@@ -388,6 +388,7 @@ __global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__rest
     const int nk = min(k, kKeep);
     const int tgt = s.tgt < nk ? s.tgt : 0;
     s.rn[tgt] = s.rnorm;
+    s.tcur = tgt;
     if (s.rebuild_to > 0) {
         if (k < s.rebuild_to) {
             // phase switch: the kept Ritz vectors still wait for exact sigmas; no
@@ -646,10 +647,22 @@ __global__ void advance_kernel(const DavProb *__restrict__ probs, DavState *__re
         st[i] = s;
         return;
     }
+    if (s.tslot >= 0 && s.tnorm2 < 1e-28 && s.tcur != 0) {
+        // the correction of a higher (competitive) root vanished: that root is
+        // resolved; no vector is added, and after a restart this iteration the
+        // last kept vector becomes the newest (its sigma is rebuilt, unchanged)
+        s.rn[s.tcur] = 0.0;
+        if (s.restart) s.newest = s.k - 1;
+        s.tslot = -1;
+        s.restart = 0;
+        st[i] = s;
+        return;
+    }
     if (s.tslot >= 0 && s.tnorm2 < 1e-28) {
-        // the correction vanished after orthogonalisation: the subspace is exhausted
+        // the correction of the lowest root vanished after orthogonalisation:
+        // the subspace is exhausted; the lowest root's own residual decides
         s.active = 0;
-        s.status = s.rnorm < r_tol ? IFCI_OK : IFCI_ERR_NOT_CONVERGED;
+        s.status = s.rn[0] < r_tol ? IFCI_OK : IFCI_ERR_NOT_CONVERGED;
         s.energy = s.theta + probs[i].e_core;
         st[i] = s;
         return;

@@ -35,6 +35,8 @@ struct DavState {
     double rnorm_exact_prev; // mixed mode, phase 1: residual norm at the previous restart
     int tgt;                 // Ritz root (rank) whose correction is built this iteration
     int skip2;               // the second Gram-Schmidt pass is not needed this iteration
+    int tcur;                // Ritz root of the correction now in flight (check -> advance)
+    int pad3_;
     double rn[4];            // last residual norm of each of the lowest Ritz roots (kKeep)
 };
 

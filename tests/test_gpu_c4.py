@@ -78,12 +78,7 @@ def test_c4_increments_are_the_moebius_inversion(fp64e_order3):
     assert out["e_total"] == pytest.approx(out["e0"] + float(np.sum(out["eps"])), abs=1e-9)
 
 
-@pytest.mark.parametrize("prec,hi,tol", [
-    ("fp64e", "fp64e", 1e-8), ("bf16", "fp64e", 1e-6),
-    pytest.param("fp64", "fp64", 1e-8, marks=pytest.mark.xfail(
-        strict=False, reason="on a few distant-body sets the FP64 trajectory settles in a higher decoupled "
-                             "charge sector (5 of 780 sets, up to 1.8e-4 Eh); the start block and root "
-                             "alternation do not guarantee the lowest sector"))])
+@pytest.mark.parametrize("prec,hi,tol", [("fp64e", "fp64e", 1e-8), ("bf16", "fp64e", 1e-6), ("fp64", "fp64", 1e-8)])
 def test_c4_order2_every_set_against_oracle(handle, chain, prec, hi, tol):
     """All 40 + 780 sets of the order-2 expansion against the oracle's energy
     of every 2-body set (tests/golden/chain40_pairs_oracle.json)."""

@@ -25,11 +25,7 @@ def _system(chain):
                              torch.tensor(chain.eri_packed(), device=DEV))
 
 
-@pytest.mark.parametrize("prec,hi,tol", [
-    ("fp64e", "fp64e", 1e-8),
-    pytest.param("fp64", "fp64", 1e-8, marks=pytest.mark.xfail(
-        strict=False, reason="four sets stay in a higher state: their lower state is not a separate block of "
-                             "the 64-function P-space, so the second pass is not triggered for it"))])
+@pytest.mark.parametrize("prec,hi,tol", [("fp64e", "fp64e", 1e-8), ("fp64", "fp64", 1e-8)])
 def test_two_pass_order2_every_set_against_oracle(prec, hi, tol):
     chain = chain_40_uneven()
     gold = json.load(open(os.path.join(GOLDEN, "chain40_pairs_oracle.json")))
