@@ -323,9 +323,10 @@ def main():
                 "traffic_note": "bytes per launch: dram read+write per G element of the ncu capture of "
                                 "oz_contract_kernel on CAS(6e,18o) x G elements per launch of this step",
                 "kernel": "oz_contract_kernel",
-                "peak_source": bf_src + " / 15 (15 BF16 slice products per FP64-accurate product)",
-                "executed_bf16_tflops": exec_step / (c_ms / 1000.0) / 1e12}
-        dtype = "f64 (BF16 tensor-core emulation)"
+                "peak_source": bf_src + " / 15 (15 FP16 slice products per FP64-accurate product; dense FP16 "
+                                        "runs at the BF16 rate)",
+                "executed_fp16_tflops": exec_step / (c_ms / 1000.0) / 1e12}
+        dtype = "f64 (FP16 tensor-core emulation)"
     else:
         lo_ms = prof["contract"][0] / steps
         hi_ms = prof["contract_hi"][0] / steps
@@ -422,7 +423,7 @@ def sigma_case(args, torch, ifci):
     if args.precision == "fp64e":
         c_ms = prof["contract_hi"][0] / steps
         line["contract_hi_tflops_algorithmic"] = fl / (c_ms / 1000.0) / 1e12
-        line["contract_hi_executed_bf16_tflops"] = executed_oz_flops(n, m) / (c_ms / 1000.0) / 1e12
+        line["contract_hi_executed_fp16_tflops"] = executed_oz_flops(n, m) / (c_ms / 1000.0) / 1e12
     print(json.dumps(line), flush=True)
     return 0
 
