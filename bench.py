@@ -305,9 +305,10 @@ def main():
     bf = peaks.get("bf16_tflops_sustained")
     bf_src = "MEASURED_PEAKS.json bf16_tflops_sustained" if bf else "fallback 1700 TFLOP/s (sustained)"
     bf = bf or 1700.0
+    fp64_peak_tf, fp64_how = _dgemm_peak(dev)
     if args.precision == "fp64":
         c_ms = prof["contract"][0] / steps
-        fp64_peak, fp64_how = _dgemm_peak(dev)
+        fp64_peak = fp64_peak_tf
         ach = flops_step / (c_ms / 1000.0) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
                 "traffic": None, "kernel": "contract_simt_kernel<double>", "peak_source": fp64_how}
@@ -348,6 +349,8 @@ def main():
         "sigma_tflops": flops_step / (sig_ms / 1000.0) / 1e12 if sig_ms > 0 else None,
         "kernel_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
         "roofline": roof,
+        "class_rooflines": class_rooflines(subs, its, {k: v[0] for k, v in prof.items()}, steps,
+                                           float(peaks.get("hbm_gbs", 6800.0)), fp64_peak_tf),
         "gpu_launches": int(launches),
         "clocks": clk,
         "e_total": out["e_total"],
@@ -375,6 +378,43 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def class_rooflines(subs, iters, kernel_ms, steps, hbm_gbs, fp64_tflops, max_space=12):
+    """Achieved rates of the per-step kernel classes other than the contraction,
+    from their CUDA-event times and algorithmic work:
+
+    * scatter (+ quantise, symmetrisation): per determinant and sigma, the G
+      values its alpha and beta lists read (2 nexc x 8 B), the quantised
+      copy read and written (16 B) and sigma read and written (16 B); HBM-bound.
+    * Davidson vector kernels: per determinant and iteration ~(5k + 8) x 8 B
+      and ~9k FP64 FMAs at an average subspace size k = (max_space + 4) / 2
+      (thick restarts keep 4 vectors); bound by the FP64 ALU on this GPU."""
+    sbytes = 0.0
+    vbytes = 0.0
+    vflops = 0.0
+    kbar = (max_space + 4) / 2.0
+    for (X, n, k), it in zip(subs, iters):
+        nd = math.comb(n, k) ** 2
+        nexc = k * (n - k + 1)
+        it = float(it)
+        sbytes += it * nd * (16.0 * nexc + 32.0)
+        vbytes += it * nd * (5.0 * kbar + 8.0) * 8.0
+        vflops += it * nd * 9.0 * kbar * 2.0
+    out = {}
+    sc_ms = (kernel_ms.get("scatter", 0.0) + kernel_ms.get("gather", 0.0)) / steps
+    if sc_ms > 0:
+        gbs = sbytes / (sc_ms / 1000.0) / 1e9
+        out["scatter"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": gbs / hbm_gbs}
+    v_ms = kernel_ms.get("vector", 0.0) / steps
+    if v_ms > 0:
+        tf = vflops / (v_ms / 1000.0) / 1e12
+        gbs = vbytes / (v_ms / 1000.0) / 1e9
+        out["davidson_vectors"] = {"bound": "fp64_alu", "achieved": tf, "peak": fp64_tflops, "unit": "TFLOP/s",
+                                   "frac": tf / fp64_tflops if fp64_tflops else None,
+                                   "hbm_gbs": gbs, "hbm_frac": gbs / hbm_gbs,
+                                   "note": "estimated k = (max_space + 4) / 2 for the subspace size"}
+    return out
 
 
 def sigma_case(args, torch, ifci):
