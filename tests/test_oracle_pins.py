@@ -406,3 +406,16 @@ def test_oracle_gradient_matches_central_differences():
         assert an == pytest.approx(fd, rel=1e-6, abs=1e-9)
         checks += 1
     assert checks == 12
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_oracle_gradient_obeys_euler_identity(order):
+    """E_iFCI(lambda h, lambda V) = lambda E_iFCI (every E_Y, E_core and E_0 is
+    an eigenvalue or energy of a Hamiltonian linear in the integrals), so
+    sum h dE/dh + sum V dE/dV = E_iFCI exactly for Hellmann–Feynman
+    derivatives: a dropped core term, a wrong expansion weight or a wrong
+    factor on the two-electron part breaks it."""
+    s = chain_4x2()
+    e, dh, dV = fci.ifci_gradient(s, order, method="dense")
+    euler = float(np.sum(s.h * dh) + np.sum(s.eri_packed() * dV))
+    assert euler == pytest.approx(e, abs=1e-10)
