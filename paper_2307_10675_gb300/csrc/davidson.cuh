@@ -24,7 +24,7 @@ struct DavState {
     int iters;               // sigma builds so far
     int status;
     int tslot;               // slot holding the correction vector
-    long long ref;           // index of the lowest-diagonal determinant (start vector)
+    long long ref;           // index of the lowest-diagonal determinant (diagnostic)
     int force;               // mixed mode: restart at the next check (subspace exhausted)
     int kold;                // subspace size just before the last restart
     int exact_all;           // mixed mode: 0 in phase 1 (low-precision sigma), 1 in phase 2 (exact sigma)

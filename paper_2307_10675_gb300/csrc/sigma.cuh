@@ -75,7 +75,7 @@ int upload_plan(ifci_handle_t h, SigmaPlan &plan, cudaStream_t s);
 int run_sigma(ifci_handle_t h, const SigmaPlan &plan, int precision, void *D, void *G, cudaStream_t s);
 size_t sigma_elem_bytes(int precision);
 
-// FP64-accurate contraction on BF16 tensor cores (sigma_oz.cu)
+// FP64-accurate contraction on FP16 tensor cores (sigma_oz.cu)
 int oz_operand_bytes(int np);                  // bytes of one problem's sliced W image (+ row scales)
 int oz_tile_n();                               // output pairs per tile
 int launch_oz_pack_w(ifci_handle_t h, int nprob, const SigmaProb *d_probs, cudaStream_t s);
