@@ -147,6 +147,125 @@ def test_h2_minimal_basis_closed_form():
         assert np.min(np.abs(w - val)) < 1e-12
 
 
+def _h2_eigenpairs():
+    """The 4 x 4 M_s = 0 CI of the H2-like model above: eigenpairs of the dense H."""
+    hgg, huu, Jgg, Juu, Jgu, K = -1.25, -0.47, 0.67, 0.70, 0.66, 0.18
+    h = np.diag([hgg, huu])
+    eri = np.zeros((2, 2, 2, 2))
+    eri[0, 0, 0, 0] = Jgg
+    eri[1, 1, 1, 1] = Juu
+    eri[0, 0, 1, 1] = eri[1, 1, 0, 0] = Jgu
+    for p, q, r, s in itertools.permutations([0, 1, 0, 1]):
+        if p != q and r != s:
+            eri[p, q, r, s] = K
+    H = fci.Hamiltonian(fci.Subsystem([], [0, 1], 1, h, eri))
+    w, v = np.linalg.eigh(H.dense())
+    return H, w, v, (hgg, huu, Jgu, K)
+
+
+def test_s_squared_h2_triplet_and_open_shell_singlet():
+    """<S^2> of the H2 eigenvectors: the level h_gg + h_uu + J_gu - K is the
+    M_s = 0 component of the triplet (S(S+1) = 2); the open-shell level
+    h_gg + h_uu + J_gu + K and both closed-shell mixtures are singlets (0).
+    A phase error in S- S+ (or an S^2 that returns 0 for every vector) fails
+    the triplet value."""
+    H, w, v, (hgg, huu, Jgu, K) = _h2_eigenpairs()
+    trip = int(np.argmin(np.abs(w - (hgg + huu + Jgu - K))))
+    sing = int(np.argmin(np.abs(w - (hgg + huu + Jgu + K))))
+    assert abs(w[trip] - (hgg + huu + Jgu - K)) < 1e-12
+    assert H.s_squared(v[:, trip]) == pytest.approx(2.0, abs=1e-12)
+    assert H.s_squared(v[:, sing]) == pytest.approx(0.0, abs=1e-12)
+    for k in range(4):
+        if k not in (trip, sing):
+            assert H.s_squared(v[:, k]) == pytest.approx(0.0, abs=1e-12)
+    # the triplet is spin-flip odd (C = -C^T), the singlets even (C = C^T)
+    C = v[:, trip].reshape(2, 2)
+    np.testing.assert_allclose(C, -C.T, atol=1e-12)
+
+
+def _fock_s_squared(n):
+    """S^2 = S- S+ + S_z (S_z + 1) from explicit Jordan–Wigner matrices on the
+    2^(2n) Fock space (alpha modes 0..n-1, beta modes n..2n-1), with
+    S+ = sum_p a+_{p alpha} a_{p beta} and S_z = (N_alpha - N_beta) / 2."""
+    nm = 2 * n
+    a = [_annihilator(nm, j) for j in range(nm)]
+    ad = [x.T.tocsr() for x in a]
+    dim = 1 << nm
+    Sp = sp.csr_matrix((dim, dim))
+    Sz = sp.csr_matrix((dim, dim))
+    for p in range(n):
+        Sp = Sp + ad[p] @ a[p + n]
+        Sz = Sz + 0.5 * (ad[p] @ a[p] - ad[p + n] @ a[p + n])
+    S2 = Sp.T @ Sp + Sz @ Sz + Sz
+    return S2.toarray()
+
+
+@pytest.mark.parametrize("ncore,nact,m", [(0, 3, 1), (1, 3, 2), (2, 2, 1), (0, 4, 2)])
+def test_s_squared_matches_fock_space_operator(ncore, nact, m):
+    """The oracle's <c|S^2|c> equals c^T S^2 c with S^2 built from explicit
+    fermion matrices (independent of the oracle's string code), for random
+    vectors c of the CI space, core orbitals included: a quadratic form that
+    agrees on random vectors is the same form.  Its polarisation
+    <u|S^2|v> = (<u+v|S^2|u+v> - <u-v|S^2|u-v>) / 4, used by the dense
+    solver inside degenerate eigenspaces, then agrees too."""
+    n = ncore + nact
+    h, eri = _random_integrals(n, seed=7 * n + m)
+    H = fci.Hamiltonian(fci.Subsystem(list(range(ncore)), list(range(ncore, n)), m, h, eri))
+    S2 = _fock_s_squared(n)
+    idx = [int(x) | (int(y) << n) for x, y in zip(H.da, H.db)]
+    S2sub = S2[np.ix_(idx, idx)]
+    # the CI space is closed under S^2 (no weight leaks out of it)
+    assert np.abs(S2[:, idx]).sum() == pytest.approx(np.abs(S2sub).sum(), abs=1e-12)
+    rng = np.random.default_rng(100 + n)
+    for _ in range(3):
+        c = rng.normal(size=H.ndet)
+        u = rng.normal(size=H.ndet)
+        assert H.s_squared(c) == pytest.approx(c @ S2sub @ c, abs=1e-10)
+        pol = 0.25 * (H.s_squared(c + u) - H.s_squared(c - u))
+        assert pol == pytest.approx(u @ S2sub @ c, abs=1e-10)
+
+
+def test_degenerate_eigenspace_spin_matches_fock_space():
+    """Two bodies with no coupling that moves charge between them and one
+    unpaired electron on each (body 0: bonding and antibonding orbitals
+    degenerate in h, no pair hopping): the lowest levels form a degenerate
+    singlet/triplet space.  Inside each degenerate eigenspace the matrix
+    <v_i|S^2|v_j> from the oracle equals the Fock-space S^2 projected on it,
+    and the dense solver's pick has S^2 = 0."""
+    n = 4
+    h = np.diag([-1.0, -1.0, -0.2, 0.9])
+    eri = np.zeros((n, n, n, n))
+    body = [0, 0, 1, 1]
+    for p, q, r, s in itertools.product(range(n), repeat=4):
+        if p == q and r == s:
+            eri[p, q, r, s] = 0.5 if body[p] == body[r] else 0.1
+    for p in range(n):                       # on-site exchange of body 1 only
+        for q in range(n):
+            if p != q and body[p] == body[q] == 1:
+                eri[p, q, q, p] = eri[p, q, p, q] = 0.05
+    H = fci.Hamiltonian(fci.Subsystem([], list(range(n)), 2, h, eri))
+    w, v = np.linalg.eigh(H.dense())
+    S2 = _fock_s_squared(n)
+    idx = [int(x) | (int(y) << n) for x, y in zip(H.da, H.db)]
+    S2sub = S2[np.ix_(idx, idx)]
+    k = 0
+    checked = 0
+    while k < len(w):
+        m = k + 1
+        while m < len(w) and w[m] - w[k] < fci.DEGENERATE_TOL:
+            m += 1
+        V = v[:, k:m]
+        for i in range(m - k):
+            for j in range(m - k):
+                pol = 0.25 * (H.s_squared(V[:, i] + V[:, j]) - H.s_squared(V[:, i] - V[:, j]))
+                assert pol == pytest.approx(V[:, i] @ S2sub @ V[:, j], abs=1e-10)
+        checked += (m - k) > 1
+        k = m
+    assert checked >= 1                      # at least one degenerate level was examined
+    e, c = fci.lowest_singlet_dense(H)
+    assert c @ S2sub @ c == pytest.approx(0.0, abs=1e-10)
+
+
 @pytest.mark.parametrize("t,U", [(1.0, 4.0), (0.3, 0.1), (1.0, 0.0)])
 def test_two_site_hubbard_closed_form(t, U):
     h = np.array([[0.0, -t], [-t, 0.0]])
