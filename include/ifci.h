@@ -51,7 +51,9 @@ typedef enum {
     IFCI_ERR_CUDA = 3,          /* a CUDA runtime call failed (message has the CUDA error) */
     IFCI_ERR_NOT_CONVERGED = 4, /* at least one problem hit max_iter; per-problem status says which */
     IFCI_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out */
-    IFCI_ERR_UNSUPPORTED = 6    /* precision or size this build does not provide */
+    IFCI_ERR_UNSUPPORTED = 6,   /* precision or size this build does not provide */
+    IFCI_SCREENED = 7           /* per-set status only: the body set was screened out
+                                   (ifci_davidson_opts_t.cnb_threshold) and not solved */
 } ifci_status_t;
 
 typedef enum {
@@ -166,9 +168,15 @@ int ifci_sigma(ifci_handle_t handle, const ifci_strings_t *str,
  *   the array; CUDA_ERR on a CUDA failure.
  * The first call on a device looks up the array's device address with that
  * device current (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Every call shares the array and each call overwrites what
- * it reads, so nothing carries over between calls — but calls that overlap
- * on the GPU (other streams, other host threads) race on the array. */
+ * stream capture.  Under CUDA's lazy module loading (the default) that first
+ * call, or the library's first kernel launch on the device, also loads the
+ * library's device code and the array itself, which takes device memory:
+ * make the first call on each device before the caller's memory manager
+ * reserves the device's memory (or load modules eagerly,
+ * CUDA_MODULE_LOADING=EAGER); later calls need no device memory at all.
+ * Every call shares the array and each call overwrites what it reads, so
+ * nothing carries over between calls — but calls that overlap on the GPU
+ * (other streams, other host threads) race on the array. */
 size_t ifci_sigma_noalloc_max_bytes(void);
 int ifci_sigma_noalloc(const ifci_strings_t *str, const double *h1, const double *eri,
                        const double *c, double *sigma, ifci_stream_t stream);
@@ -248,6 +256,24 @@ typedef struct {
                             second block within 0.3 Eh of the lowest are solved again
                             from that block's lowest vector, and the lower result (energy
                             and vector) is kept; 0 or 1: one pass (default 0). */
+    double decouple_tol; /* > 0: orbitals that no integral couples above this (|h_pq|, and
+                            max_rs |(pq|rs)| for p, q in different groups) split a problem into
+                            groups; H without those integrals conserves the alpha and beta
+                            electron counts of every group, and each such block is solved as
+                            its own Davidson problem (all blocks of a space share one sigma
+                            per iteration); the lowest block's vector then starts a Davidson
+                            iteration with the full H.  The lowest eigenvalue over decoupled
+                            sectors is thereby found by construction.  0: off.
+                            (default 1e-5) */
+    double cnb_threshold;/* ifci_increments / ifci_rdm_backward only.  > 0: connected n-body
+                            screening of the body sets of 3 or more bodies (Methods, screening
+                            paragraph, C = 10^-4.6 Ha there; the exact rule is in the paper's
+                            Supplementary Information, not available): a set is solved only
+                            when its bodies are connected through pairs {a, b} of it with
+                            |eps_ab| >= cnb_threshold; a screened set has eps_X = 0 in Eqs.
+                            2-5 (which are then taken recursively, screened increments
+                            counting as zero), e_x = NaN and status IFCI_SCREENED.
+                            0: every set is solved (default 0). */
 } ifci_davidson_opts_t;
 
 /* Fills opts with the defaults listed above (precision IFCI_FP64). */
@@ -283,11 +309,12 @@ int ifci_num_subsets(int nbody, int max_order, long long *count);
 
 /* ifci_increments — the iFCI expansion truncated at max_order (Eqs. 1-5).
  *   e0      : host double*, reference energy E_0.
- *   e_x     : host double[nsub] or NULL, E_X per body set.
+ *   e_x     : host double[nsub] or NULL, E_X per body set (NaN if screened).
  *   eps     : host double[nsub], increments eps_X.
  *   e_total : host double*, E_0 + sum eps_X.
  *   iters   : host int[nsub] or NULL, sigma builds per set.
- *   status  : host int[nsub] or NULL, per-set Davidson status.
+ *   status  : host int[nsub] or NULL, per-set Davidson status (IFCI_SCREENED for a
+ *             set left out by opts->cnb_threshold).
  * Keeps the converged vectors in the handle when opts->refine >= 0 so that
  * ifci_rdm_backward can reuse them.  Synchronous. */
 int ifci_increments(ifci_handle_t handle, const ifci_system_t *sys, int max_order,
@@ -300,7 +327,10 @@ int ifci_increments(ifci_handle_t handle, const ifci_system_t *sys, int max_orde
  *   dE/dV[A][B] = grad_out * 1/2 sum over ordered (p,q) in A, (r,s) in B of
  *                 [sum_Y w_Y Gamma^Y_pqrs + (1 - sum w) Gamma^0_pqrs]
  * with w_Y = (-1)^(n-|Y|) C(N-|Y|-1, n-|Y|), gamma/Gamma the spin-summed
- * full-space 1-/2-RDMs of E_Y's vector.  dh: device double[norb*norb];
+ * full-space 1-/2-RDMs of E_Y's vector.  Under connected n-body screening
+ * (opts->cnb_threshold > 0) w_Y is the derivative of the screened total
+ * with respect to E_Y at the inclusion pattern of the forward call (the
+ * pattern itself is held fixed).  dh: device double[norb*norb];
  * deri: device double[npair*npair]; both overwritten.
  * recompute_vectors = 0 reuses the vectors of the last ifci_increments on
  * this handle for the same system (INVALID_ARG if there are none).

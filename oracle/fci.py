@@ -390,15 +390,55 @@ def increments_from_correlation(ec: Dict[Tuple[int, ...], float]) -> Dict[Tuple[
 
 
 def ifci_energies(system, max_order: int, method: str = "auto", tol: float = 1e-9,
-                  subsets: Optional[List[Tuple[int, ...]]] = None):
-    """E_0, {X: E_X}, {X: eps_X} and E_iFCI = E_0 + sum eps (Eq. 1 truncated at max_order)."""
+                  subsets: Optional[List[Tuple[int, ...]]] = None, cnb: float = 0.0):
+    """E_0, {X: E_X}, {X: eps_X} and E_iFCI = E_0 + sum eps (Eq. 1 truncated at max_order).
+
+    ``cnb`` > 0 applies the connected n-body screening to the sets of three
+    or more bodies (Methods, screening paragraph; see ``cnb_connected``):
+    a screened set is not solved, has no entry in the E_X map, and its
+    increment is 0 in the recursion of Eqs. 2-5 and in the total."""
     e0 = reference_energy(system)
     subs = subsets if subsets is not None else body_subsets(system.nbody, max_order)
-    ex = {X: solve_subsystem(system, X, method, tol).energy for X in subs}
-    ec = {X: ex[X] - e0 for X in subs}
-    eps = increments_from_correlation(ec)
+    if cnb <= 0.0:
+        ex = {X: solve_subsystem(system, X, method, tol).energy for X in subs}
+        ec = {X: ex[X] - e0 for X in subs}
+        eps = increments_from_correlation(ec)
+        total = e0 + sum(eps.values())
+        return e0, ex, eps, total
+    ex: Dict[Tuple[int, ...], float] = {}
+    eps: Dict[Tuple[int, ...], float] = {}
+    for k in sorted({len(X) for X in subs}):
+        for X in [Y for Y in subs if len(Y) == k]:
+            if k >= 3 and not cnb_connected(X, eps, cnb):
+                eps[X] = 0.0
+                continue
+            ex[X] = solve_subsystem(system, X, method, tol).energy
+            val = ex[X] - e0
+            for j in range(1, k):
+                for Y in itertools.combinations(X, j):
+                    val -= eps[Y]
+            eps[X] = val
     total = e0 + sum(eps.values())
     return e0, ex, eps, total
+
+
+def cnb_connected(X: Tuple[int, ...], eps: Dict[Tuple[int, ...], float], C: float) -> bool:
+    """Connected n-body screening (Methods, screening paragraph: terms with
+    n >= 3 are kept by a connectivity argument with threshold C; the exact rule
+    is in the paper's Supplementary Information, which is not available).
+    Reading used here: the bodies of X are the vertices of a graph whose
+    edges are the pairs {a, b} of X with |eps_ab| >= C; X is kept when that
+    graph is connected (for three bodies: at least two of the three pairs)."""
+    X = tuple(sorted(X))
+    seen = {X[0]}
+    stack = [X[0]]
+    while stack:
+        a = stack.pop()
+        for b in X:
+            if b not in seen and abs(eps[tuple(sorted((a, b)))]) >= C:
+                seen.add(b)
+                stack.append(b)
+    return len(seen) == len(X)
 
 
 # --------------------------------------------------------------------------

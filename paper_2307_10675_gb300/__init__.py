@@ -4,7 +4,7 @@ The compute path is the CUDA library ``_build/libifci.so`` (C ABI in
 ``include/ifci.h``); this package only marshals arguments to it.
 """
 from .api import (  # noqa: F401
-    IFCI_BF16, IFCI_FP32, IFCI_FP64, IFCI_FP64E, IFCI_TF32, PRECISIONS,
+    IFCI_BF16, IFCI_FP32, IFCI_FP64, IFCI_FP64E, IFCI_TF32, IFCI_SCREENED, PRECISIONS,
     CIProblem, Handle, IfciEnergy, IfciError, StringTables, SystemArrays, ifci_energy,
     body_subsets, davidson_opts,
     ifci_build_strings, ifci_davidson_batched, ifci_frozen_core, ifci_h_elements, ifci_hdiag, ifci_increments,

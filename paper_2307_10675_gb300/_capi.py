@@ -19,6 +19,7 @@ IFCI_ERR_CUDA = 3
 IFCI_ERR_NOT_CONVERGED = 4
 IFCI_ERR_TIMEOUT = 5
 IFCI_ERR_UNSUPPORTED = 6
+IFCI_SCREENED = 7
 
 IFCI_FP64, IFCI_FP32, IFCI_TF32, IFCI_BF16, IFCI_FP64E = 0, 1, 2, 3, 4
 IFCI_SIGMA_SPIN_SYMMETRIC = 0x100
@@ -51,7 +52,8 @@ class Problem(ctypes.Structure):
 class DavidsonOpts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("max_iter", c_int), ("max_space", c_int), ("e_tol", c_double),
                 ("r_tol", c_double), ("refine", c_int), ("hi_precision", c_int), ("det_budget", c_ll),
-                ("graph_iters", c_int), ("sector_passes", c_int)]
+                ("graph_iters", c_int), ("sector_passes", c_int), ("decouple_tol", c_double),
+                ("cnb_threshold", c_double)]
 
 
 def lib_path() -> str:

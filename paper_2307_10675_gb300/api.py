@@ -15,7 +15,7 @@ import numpy as np
 import torch
 
 from . import _capi
-from ._capi import (IFCI_BF16, IFCI_ERR_NOT_CONVERGED, IFCI_FP32, IFCI_FP64, IFCI_FP64E, IFCI_OK,  # noqa: F401
+from ._capi import (IFCI_BF16, IFCI_ERR_NOT_CONVERGED, IFCI_FP32, IFCI_FP64, IFCI_FP64E, IFCI_OK, IFCI_SCREENED,  # noqa: F401
                     IFCI_TF32)
 
 PRECISIONS = {"fp64": IFCI_FP64, "fp32": IFCI_FP32, "tf32": IFCI_TF32, "bf16": IFCI_BF16, "fp64e": IFCI_FP64E}

@@ -20,6 +20,10 @@ struct ifci_handle_s {
     char *ws = nullptr;          // workspace base (device)
     size_t ws_bytes = 0;         // capacity
     size_t ws_top = 0;           // bump pointer
+    // the Davidson solver's own workspace, swapped in for the duration of a
+    // solve (DavArena) so that it can grow after the caller carved its part
+    char *ws_alt = nullptr;
+    size_t ws_alt_bytes = 0, ws_alt_top = 0;
     std::string last_error;
     long long launches = 0;
     int *d_err = nullptr;        // device flag set by kernels whose bounded waits ran out
@@ -33,6 +37,8 @@ struct ifci_handle_s {
         double *vec = nullptr;               // device, all vectors back to back
         size_t vec_bytes = 0;
         std::vector<long long> vec_off;      // per subset offset (doubles)
+        bool screened = false;               // connected n-body screening was applied
+        std::vector<char> included;          // per subset: solved (1) or screened out (0)
     } kept;
 };
 
@@ -111,6 +117,21 @@ T *ws_take(ifci_handle_t h, size_t count) {
     return p;
 }
 inline size_t ws_round(size_t bytes) { return (bytes + 255) & ~size_t(255); }
+
+// Makes the handle's Davidson workspace the current one (ws_reserve, ws_take)
+// for its lifetime; the caller's workspace and the pointers into it stay valid.
+struct DavArena {
+    ifci_handle_t h;
+    explicit DavArena(ifci_handle_t h_) : h(h_) { swap(); }
+    ~DavArena() { swap(); }
+    DavArena(const DavArena &) = delete;
+    DavArena &operator=(const DavArena &) = delete;
+    void swap() {
+        char *b = h->ws; h->ws = h->ws_alt; h->ws_alt = b;
+        size_t t = h->ws_bytes; h->ws_bytes = h->ws_alt_bytes; h->ws_alt_bytes = t;
+        t = h->ws_top; h->ws_top = h->ws_alt_top; h->ws_alt_top = t;
+    }
+};
 
 inline cudaStream_t as_cuda(ifci_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
 

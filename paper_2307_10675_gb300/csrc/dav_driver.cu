@@ -1,7 +1,19 @@
-// Host driver of the batched Davidson: workspace layout, string tables per
-// (norb, nelec_spin) class, folded matrices, diagonals, and the C entry point.
+// Host driver of the batched Davidson: sector decomposition, workspace layout,
+// string tables per (norb, nelec_spin) class, folded matrices, diagonals, and
+// the C entry point.
+//
+// A solve is organised in sigma units and Davidson problems.  A unit is one
+// CI space with its own sigma build; a problem iterates in one block of a
+// unit's space.  A unit whose orbitals form one coupled group has a single
+// problem, the whole space.  A unit whose orbitals split into decoupled
+// groups (sectors.cu) has one problem per block of H' (the distributions of
+// the alpha and beta electrons among the groups, taken with their spin-flip
+// images); the lowest block's vector then starts a second run with the full
+// H on the whole space (the polish), whose result is the unit's answer.
 #include <algorithm>
+#include <cmath>
 #include <map>
+#include <unordered_map>
 
 #include "dav_driver.cuh"
 #include "hamiltonian.cuh"
@@ -11,63 +23,397 @@ namespace ifci {
 
 int launch_convert_w(ifci_handle_t h, int nprob, const SigmaProb *d_probs, cudaStream_t s);
 
-static void dav_layout(const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o, DavSizes &z) {
-    z = DavSizes{};
-    std::map<std::pair<int, int>, int> cls;
-    const int ms = o.max_space;
-    const bool lo = o.precision == IFCI_FP32 || o.precision == IFCI_TF32 || o.precision == IFCI_BF16;
-    const bool tc = o.precision == IFCI_BF16 || o.precision == IFCI_TF32;
-    const bool oz = hi_precision_of(o) == IFCI_FP64E;
-    const size_t eb_lo = sigma_elem_bytes(o.precision);
-    for (const ProbSpec &p : specs) {
-        int nstr = (int)binom(p.n, p.m), nexc = p.m * (p.n - p.m + 1);
-        long long ndet = (long long)nstr * nstr;
-        int np = p.n * (p.n + 1) / 2;
-        if (!cls.count({p.n, p.m})) {
-            cls[{p.n, p.m}] = (int)cls.size();
-            z.bytes += ws_round((size_t)nstr * 8) + ws_round((size_t)nstr * nexc * 4) +
-                       ws_round((size_t)nstr * kBlk16Stride);
-            if (tc || oz) z.bytes += ws_round((size_t)nstr * pmap_ld(np) * 4);   // pair map
+namespace {
+
+// one Davidson problem of a run: a block of one unit's space
+struct BlockSpec {
+    int unit;
+    int na, nb, sym;
+    int sa_off, sb_off;      // offsets into the run's string-index list; -1: every string in order
+    long long ndet, ndim;
+};
+
+// one sigma unit of a run
+struct Unit {
+    ProbSpec spec;           // the CI space (its integrals are the full H)
+    const double *h1, *eri;  // integrals of the Hamiltonian iterated (H' for a sectored unit)
+    bool sector;             // several blocks share the unit's sigma
+    const double *seed;      // start vector of the whole space, or nullptr
+    int prob0, nprob;
+    double *expand_to;       // sectored unit: whole-space target of the lowest block's vector, or nullptr
+};
+
+// Counts (count = true) or takes (count = false) workspace pieces in one order.
+struct Carver {
+    ifci_handle_t h;
+    bool count;
+    size_t total = 0;
+    bool ok = true;
+    template <typename T>
+    T *take(size_t n) {
+        if (count) {
+            total += ws_round(std::max<size_t>(n, 1) * sizeof(T));
+            return reinterpret_cast<T *>(alignof(T) > 256 ? alignof(T) : 256);
         }
-        z.bytes += ws_round((size_t)np * np * 8);                       // W
-        if (lo) z.bytes += ws_round((size_t)np * np * 4);               // Wf
-        if (tc) z.bytes += ws_round((size_t)tc_operand_bytes(np, o.precision));
-        if (oz) z.bytes += ws_round((size_t)oz_operand_bytes(np));
-        z.bytes += ws_round((size_t)ndet * 8);                          // hd
-        z.bytes += 2 * ws_round((size_t)(ms + 1) * ndet * 8);           // B, S
-        z.nitem += (int)((ndet + kVecChunk - 1) / kVecChunk);
-        z.max_pd = std::max(z.max_pd, sigma_elems(np, ndet));
-        z.sum_pd += sigma_elems(np, ndet);
-        z.n_items_sigma += (ndet + kGatherChunk - 1) / kGatherChunk;
-        z.n_tiles_sigma += ((np + kGemmTM - 1) / kGemmTM) * ((ndet + kGemmTN - 1) / kGemmTN) +
-                           tcg::row_tile_count(nstr) * ((np + oz_tile_n() - 1) / oz_tile_n() + 1);
+        T *p = ws_take<T>(h, std::max<size_t>(n, 1));
+        if (!p) ok = false;
+        return p;
     }
-    size_t n = specs.size();
-    z.nclass = (int)cls.size();
-    long long budget = o.det_budget > 0 ? o.det_budget : (1ll << 31);   // two 16 GB intermediates
-    budget = std::max(budget, z.max_pd);
-    budget = std::min(budget, std::max(z.sum_pd, z.max_pd));
-    z.budget = budget;
-    size_t eb = 8;  // FP64 sigma is always needed (hi path); the lo buffers share it
-    (void)eb_lo;
-    z.bytes += 2 * ws_round((size_t)budget * eb);                          // D, G
-    z.bytes += ws_round(n * sizeof(DavProb)) + ws_round(n * sizeof(DavState)) + ws_round(z.nitem * sizeof(WorkItem));
-    z.bytes += ws_round((size_t)z.nitem * kNP * 8) + ws_round(n * kMaxSpace * kMaxSpace * 8) +
-               ws_round(n * kYStride * 8) + ws_round(n * kNP * 8) + ws_round(8) + 2 * ws_round(n * 4);
-    z.bytes += ws_round(n * sizeof(FoldDesc)) + ws_round(n * sizeof(HdiagDesc)) + psp_workspace_bytes((int)n) +
-               ws_round(n * 2 * sizeof(double));
-    z.bytes += ws_round((size_t)z.nitem * sizeof(int)) + ws_round((size_t)z.nitem * sizeof(long long));
-    // two sigma plans (hi and lo)
-    z.bytes += 2 * (ws_round(n * sizeof(SigmaProb)) + ws_round((size_t)z.n_items_sigma * sizeof(WorkItem)) +
-                    2 * ws_round((size_t)z.n_tiles_sigma * sizeof(WorkItem)));
-    z.bytes += 4096;
+};
+
+std::vector<uint32_t> host_strings(int n, int m) {
+    std::vector<uint32_t> out;
+    uint64_t v = (1ull << m) - 1ull;
+    const uint64_t lim = 1ull << n;
+    while (v < lim) {
+        out.push_back((uint32_t)v);
+        const uint64_t t = v | (v - 1);
+        v = (t + 1) | (((~t & (t + 1)) - 1) >> (__builtin_ctzll(v) + 1));
+    }
+    return out;
 }
 
-size_t dav_workspace_bytes(const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o) {
-    DavSizes z;
-    dav_layout(specs, o, z);
-    return z.bytes;
+// Runs one batch of units and their problems to convergence.  Problem
+// results land in hs (DavState per problem); blk (optional) gets the two
+// lowest P-space block energies per problem; sectored units with expand_to
+// receive their lowest block's vector as a whole-space vector.
+int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSpec> &blocks,
+            const std::vector<int> &sidx, const ifci_davidson_opts_t &o, cudaStream_t s, std::vector<DavState> &hs,
+            std::vector<double> *blk) {
+    const int nu = (int)units.size(), n = (int)blocks.size();
+    const bool lo = o.precision == IFCI_FP32 || o.precision == IFCI_TF32 || o.precision == IFCI_BF16;
+    const bool tc = o.precision == IFCI_BF16 || o.precision == IFCI_TF32;
+    const int hi_prec = hi_precision_of(o);
+    const bool oz = hi_prec == IFCI_FP64E;
+    const int ms = o.max_space;
+
+    // ---- host-side layout: string classes, vector items, hdiag work, sigma plans
+    std::map<std::pair<int, int>, int> cls;
+    std::vector<std::pair<int, int>> cls_keys;
+    for (const Unit &u : units) {
+        auto key = std::make_pair(u.spec.n, u.spec.m);
+        if (!cls.count(key)) {
+            int nstr = 0, nexc = 0;
+            if (ifci_string_counts(u.spec.n, u.spec.m, &nstr, &nexc) != IFCI_OK || u.spec.m < 1)
+                return set_error(h, IFCI_ERR_INVALID_ARG, "davidson: problem with norb=%d nelec_spin=%d", u.spec.n,
+                                 u.spec.m);
+            cls[key] = (int)cls_keys.size();
+            cls_keys.push_back(key);
+        }
+    }
+    DavBatch b;
+    b.nprob = n;
+    b.nunit = nu;
+    b.max_space = ms;
+    b.keep = std::min(kKeep, ms - 2);
+    b.precision = o.precision;
+    b.hi_precision = hi_prec;
+    b.max_iter = o.max_iter;
+    b.graph_iters = o.graph_iters > 0 ? o.graph_iters : 0;
+    b.e_tol = o.e_tol;
+    b.r_tol = o.r_tol;
+    std::vector<int> item0(n), nitem(n);
+    for (int i = 0; i < n; i++) {
+        item0[i] = (int)b.vitems.size();
+        for (long long s0 = 0; s0 < blocks[i].ndet; s0 += kVecChunk) b.vitems.push_back(WorkItem{i, 0, s0});
+        nitem[i] = (int)b.vitems.size() - item0[i];
+    }
+    std::vector<int> hw_prob;
+    std::vector<long long> hw_start;
+    long long max_pd = 0, sum_pd = 0;
+    SigmaPlan hi, lop;
+    for (int u = 0; u < nu; u++) {
+        const ProbSpec &p = units[u].spec;
+        const int nstr = (int)binom(p.n, p.m), nexc = p.m * (p.n - p.m + 1), np = p.n * (p.n + 1) / 2;
+        const long long ndet = (long long)nstr * nstr;
+        for (long long s0 = 0; s0 < ndet; s0 += kVecChunk) {
+            hw_prob.push_back(u);
+            hw_start.push_back(s0);
+        }
+        max_pd = std::max(max_pd, sigma_elems(np, ndet));
+        sum_pd += sigma_elems(np, ndet);
+        SigmaProb sp{};
+        sp.n = p.n; sp.nstr = nstr; sp.nexc = nexc; sp.np = np; sp.ld = np;
+        sp.ndet = ndet; sp.stride = ndet;
+        sp.sym = ((tc || oz) && 2ll * nstr * nstr < (1ll << 31)) ? 1 : 0;   // plan_sigma keeps it for tensor cores
+        sp.dscale = 2.0;   // basis vectors are normalised: |D| <= 2
+        hi.probs.push_back(sp);
+        lop.probs.push_back(sp);
+    }
+    long long budget = o.det_budget > 0 ? o.det_budget : (1ll << 31);   // two 16 GB intermediates
+    budget = std::max(budget, max_pd);
+    budget = std::min(budget, std::max(sum_pd, max_pd));
+    IFCI_TRY(plan_sigma(h, hi, budget, hi_prec));
+    if (lo) IFCI_TRY(plan_sigma(h, lop, budget * 8 / (long long)sigma_elem_bytes(o.precision), o.precision));
+
+    // ---- device memory, counted then taken in the same order
+    struct Mem {
+        std::vector<uint64_t *> st;
+        std::vector<int32_t *> ex;
+        std::vector<uint8_t *> bl;
+        std::vector<int32_t *> pm;
+        std::vector<double *> W, gc, gs;
+        std::vector<float *> Wf;
+        std::vector<void *> Wtc;
+        std::vector<char *> Woz;
+        std::vector<double *> hd, B, S, cblk;
+        int *sidx = nullptr;
+        DavProb *probs = nullptr;
+        DavState *state = nullptr;
+        WorkItem *vitems = nullptr;
+        double *part = nullptr, *gsm = nullptr, *y = nullptr, *coef = nullptr, *blk = nullptr;
+        int *nactive = nullptr, *dhi = nullptr, *dlo = nullptr;
+        int2 *urange = nullptr;
+        int *uhi = nullptr, *ulo = nullptr;
+        FoldDesc *fold = nullptr;
+        HdiagDesc *hdu = nullptr, *hdp = nullptr;
+        int *hwp = nullptr;
+        long long *hws = nullptr;
+        double **dst = nullptr;
+        void *D = nullptr, *G = nullptr;
+        SigmaProb *hi_p = nullptr, *lo_p = nullptr;
+        WorkItem *hi_i = nullptr, *hi_t = nullptr, *hi_c = nullptr, *lo_i = nullptr, *lo_t = nullptr, *lo_c = nullptr;
+        long long *pidx = nullptr;
+        int *pcount = nullptr;
+    };
+    auto carve = [&](Carver &c, Mem &m) {
+        const int nc = (int)cls_keys.size();
+        m.st.resize(nc); m.ex.resize(nc); m.bl.resize(nc); m.pm.assign(nc, nullptr);
+        for (int k = 0; k < nc; k++) {
+            const int nn = cls_keys[k].first, mm = cls_keys[k].second;
+            const int nstr = (int)binom(nn, mm), nexc = mm * (nn - mm + 1), np = nn * (nn + 1) / 2;
+            m.st[k] = c.take<uint64_t>(nstr);
+            m.ex[k] = c.take<int32_t>((size_t)nstr * nexc);
+            m.bl[k] = c.take<uint8_t>((size_t)nstr * kBlk16Stride);
+            // Davidson vectors are spin-flip symmetric: the tensor-core sigmas use
+            // the alpha-only gathers where the pair map's offsets fit in int32
+            if ((tc || oz) && 2ll * nstr * nstr < (1ll << 31)) m.pm[k] = c.take<int32_t>((size_t)nstr * pmap_ld(np));
+        }
+        m.W.resize(nu); m.Wf.assign(nu, nullptr); m.Wtc.assign(nu, nullptr); m.Woz.assign(nu, nullptr);
+        m.gc.assign(nu, nullptr); m.gs.assign(nu, nullptr);
+        for (int u = 0; u < nu; u++) {
+            const ProbSpec &p = units[u].spec;
+            const int np = p.n * (p.n + 1) / 2;
+            const long long ndet = binom(p.n, p.m) * binom(p.n, p.m);
+            m.W[u] = c.take<double>((size_t)np * np);
+            if (lo) m.Wf[u] = c.take<float>((size_t)np * np);
+            if (tc) m.Wtc[u] = c.take<char>(tc_operand_bytes(np, o.precision));
+            if (oz) m.Woz[u] = c.take<char>(oz_operand_bytes(np));
+            if (units[u].sector) {
+                m.gc[u] = c.take<double>(ndet);
+                m.gs[u] = c.take<double>(ndet);
+            }
+        }
+        m.hd.resize(n); m.B.resize(n); m.S.resize(n); m.cblk.assign(n, nullptr);
+        for (int i = 0; i < n; i++) {
+            const long long nd = blocks[i].ndet;
+            m.hd[i] = c.take<double>(nd);
+            m.B[i] = c.take<double>((size_t)(ms + 1) * nd);
+            m.S[i] = c.take<double>((size_t)(ms + 1) * nd);
+            if (units[blocks[i].unit].sector && units[blocks[i].unit].expand_to) m.cblk[i] = c.take<double>(nd);
+        }
+        m.sidx = c.take<int>(sidx.size());
+        m.probs = c.take<DavProb>(n);
+        m.state = c.take<DavState>(n);
+        m.vitems = c.take<WorkItem>(b.vitems.size());
+        m.part = c.take<double>(b.vitems.size() * kNP);
+        m.gsm = c.take<double>((size_t)n * kMaxSpace * kMaxSpace);
+        m.y = c.take<double>((size_t)n * kYStride);
+        m.coef = c.take<double>((size_t)n * kNP);
+        m.nactive = c.take<int>(2);
+        m.blk = c.take<double>((size_t)n * 2);
+        m.dhi = c.take<int>(n);
+        m.dlo = c.take<int>(n);
+        m.urange = c.take<int2>(nu);
+        m.uhi = c.take<int>(nu);
+        m.ulo = c.take<int>(nu);
+        m.fold = c.take<FoldDesc>(nu);
+        m.hdu = c.take<HdiagDesc>(nu);
+        m.hdp = c.take<HdiagDesc>(n);
+        m.hwp = c.take<int>(hw_prob.size());
+        m.hws = c.take<long long>(hw_start.size());
+        m.dst = c.take<double *>(n);
+        m.D = c.take<char>((size_t)budget * 8);
+        m.G = c.take<char>((size_t)budget * 8);
+        m.hi_p = c.take<SigmaProb>(hi.probs.size());
+        m.hi_i = c.take<WorkItem>(hi.items.size());
+        m.hi_t = c.take<WorkItem>(hi.tiles.size());
+        m.hi_c = c.take<WorkItem>(hi.tctiles.size());
+        if (lo) {
+            m.lo_p = c.take<SigmaProb>(lop.probs.size());
+            m.lo_i = c.take<WorkItem>(lop.items.size());
+            m.lo_t = c.take<WorkItem>(lop.tiles.size());
+            m.lo_c = c.take<WorkItem>(lop.tctiles.size());
+        }
+        m.pidx = c.take<long long>((size_t)n * kPspMax);
+        m.pcount = c.take<int>(n);
+    };
+    Mem mem;
+    {
+        Carver cnt{h, true};
+        carve(cnt, mem);
+        IFCI_TRY(ws_reserve(h, cnt.total + 4096));
+    }
+    Carver real{h, false};
+    carve(real, mem);
+    if (!real.ok) return set_error(h, IFCI_ERR_OOM, "davidson: workspace");
+
+    // ---- string tables
+    for (size_t k = 0; k < cls_keys.size(); k++) {
+        const int nn = cls_keys[k].first, mm = cls_keys[k].second;
+        const int nstr = (int)binom(nn, mm), nexc = mm * (nn - mm + 1), np = nn * (nn + 1) / 2;
+        IFCI_TRY(ifci_build_strings(h, nn, mm, mem.st[k], mem.ex[k], (ifci_stream_t)s));
+        IFCI_TRY(launch_exc_blocks(h, nstr, nexc, mem.ex[k], mem.bl[k], s));
+        if (mem.pm[k]) IFCI_TRY(launch_pair_map(h, nstr, nexc, np, mem.ex[k], mem.pm[k], s));
+    }
+
+    // ---- descriptors
+    std::vector<FoldDesc> folds(nu);
+    std::vector<HdiagDesc> hdu(nu), hdp(n);
+    std::vector<int2> urange(nu);
+    for (int u = 0; u < nu; u++) {
+        const Unit &U = units[u];
+        const ProbSpec &p = U.spec;
+        const int k = cls[{p.n, p.m}];
+        const int nstr = (int)binom(p.n, p.m);
+        const int np = p.n * (p.n + 1) / 2;
+        folds[u] = FoldDesc{p.n, 2 * p.m, np, U.h1, U.eri, mem.W[u]};
+        // whole-space diagonal: straight into the single problem's hd, or into gs
+        // (then gathered per block)
+        hdu[u] = HdiagDesc{p.n, nstr, mem.st[k], U.h1, U.eri, U.sector ? mem.gs[u] : mem.hd[U.prob0]};
+        urange[u] = make_int2(U.prob0, U.nprob);
+        for (SigmaPlan *pl : {&hi, &lop}) {
+            SigmaProb &sp = pl->probs[u];
+            sp.exc = mem.ex[k];
+            sp.blk = mem.bl[k];
+            sp.pmap = mem.pm[k];
+            if (!sp.pmap) sp.sym = 0;
+            sp.W = mem.W[u]; sp.Wf = mem.Wf[u]; sp.Wtc = mem.Wtc[u];
+            sp.Woz = mem.Woz[u];
+            sp.Wexp = oz ? (double *)(mem.Woz[u] + (oz_operand_bytes(np) - np * 8 - 256)) : nullptr;
+            if (U.sector) {
+                sp.cbase = mem.gc[u]; sp.sbase = mem.gs[u];
+                sp.cslot = nullptr; sp.sslot = nullptr;
+            } else {
+                sp.cbase = mem.B[U.prob0]; sp.sbase = mem.S[U.prob0];
+                sp.cslot = &mem.state[U.prob0].newest;
+                sp.sslot = &mem.state[U.prob0].newest;
+            }
+            sp.active = (pl == &hi ? mem.uhi : mem.ulo) + u;
+        }
+    }
+    for (int i = 0; i < n; i++) {
+        const BlockSpec &bs = blocks[i];
+        const Unit &U = units[bs.unit];
+        const ProbSpec &p = U.spec;
+        const int k = cls[{p.n, p.m}];
+        DavProb dp{};
+        dp.ndet = bs.ndet;
+        dp.ndim = bs.ndim;
+        dp.nstr = (int)binom(p.n, p.m);
+        dp.na = bs.na;
+        dp.nb = bs.nb;
+        dp.sym = bs.sym;
+        dp.item0 = item0[i];
+        dp.nitem = nitem[i];
+        dp.seed_block = p.seed_block;
+        dp.sa = bs.sa_off >= 0 ? mem.sidx + bs.sa_off : nullptr;
+        dp.sb = bs.sb_off >= 0 ? mem.sidx + bs.sb_off : nullptr;
+        dp.B = mem.B[i];
+        dp.S = mem.S[i];
+        dp.hd = mem.hd[i];
+        dp.c_out = U.sector ? mem.cblk[i] : p.c_out;
+        dp.seed = U.seed;
+        dp.gc = U.sector ? mem.gc[bs.unit] : nullptr;
+        dp.gs = U.sector ? mem.gs[bs.unit] : nullptr;
+        dp.e_core = p.e_core;
+        b.probs.push_back(dp);
+        hdp[i] = HdiagDesc{p.n, dp.nstr, mem.st[k], U.h1, U.eri, mem.hd[i]};
+    }
+    b.d_probs = mem.probs;
+    b.d_state = mem.state;
+    b.d_vitems = mem.vitems;
+    b.d_part = mem.part;
+    b.d_gs = mem.gsm;
+    b.d_y = mem.y;
+    b.d_coef = mem.coef;
+    b.d_nactive = mem.nactive;
+    b.d_blk_energy = mem.blk;
+    b.d_urange = mem.urange;
+    b.d_uhi = mem.uhi;
+    b.d_ulo = mem.ulo;
+    b.any_sector = false;
+    for (const Unit &U : units) b.any_sector = b.any_sector || U.sector;
+    hi.d_probs = mem.hi_p; hi.d_items = mem.hi_i; hi.d_tiles = mem.hi_t; hi.d_tctiles = mem.hi_c;
+    IFCI_TRY(upload_plan_to(h, hi, s));
+    if (lo) {
+        lop.d_probs = mem.lo_p; lop.d_items = mem.lo_i; lop.d_tiles = mem.lo_t; lop.d_tctiles = mem.lo_c;
+        IFCI_TRY(upload_plan_to(h, lop, s));
+    }
+    if (!sidx.empty())
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.sidx, sidx.data(), sidx.size() * 4, cudaMemcpyHostToDevice, s));
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.fold, folds.data(), nu * sizeof(FoldDesc), cudaMemcpyHostToDevice, s));
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.hdu, hdu.data(), nu * sizeof(HdiagDesc), cudaMemcpyHostToDevice, s));
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.hdp, hdp.data(), n * sizeof(HdiagDesc), cudaMemcpyHostToDevice, s));
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.urange, urange.data(), nu * sizeof(int2), cudaMemcpyHostToDevice, s));
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.hwp, hw_prob.data(), hw_prob.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.hws, hw_start.data(), hw_start.size() * sizeof(long long),
+                                     cudaMemcpyHostToDevice, s));
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(b.d_probs, b.probs.data(), n * sizeof(DavProb), cudaMemcpyHostToDevice, s));
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(b.d_vitems, b.vitems.data(), b.vitems.size() * sizeof(WorkItem),
+                                     cudaMemcpyHostToDevice, s));
+    IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_gs, 0, (size_t)n * kMaxSpace * kMaxSpace * 8, s));
+    IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_y, 0, (size_t)n * kYStride * 8, s));
+    int maxnp = 0;
+    for (const Unit &U : units) maxnp = std::max(maxnp, U.spec.n * (U.spec.n + 1) / 2);
+    IFCI_TRY(launch_fold(h, nu, mem.fold, maxnp, s));
+    if (lo) IFCI_TRY(launch_convert_w(h, nu, lop.d_probs, s));
+    if (tc) IFCI_TRY(launch_tc_pack_w(h, nu, lop.d_probs, o.precision, s));
+    if (oz) IFCI_TRY(launch_oz_pack_w(h, nu, hi.d_probs, s));
+    IFCI_TRY(launch_hdiag(h, mem.hdu, mem.hwp, mem.hws, (int)hw_prob.size(), kVecChunk, s));
+    if (b.any_sector) IFCI_TRY(launch_sector_hd(h, b, s));
+    b.d_pidx = mem.pidx;
+    b.d_pcount = mem.pcount;
+    IFCI_TRY(dav_init(h, b, mem.hdp, s));
+
+    int *h_nactive = nullptr;
+    IFCI_CUDA_TRY(h, cudaMallocHost(&h_nactive, 2 * sizeof(int)));
+    int st = dav_iterate(h, b, hi, lo ? &lop : nullptr, mem.dhi, mem.dlo, mem.D, mem.G, h_nactive, s);
+    cudaFreeHost(h_nactive);
+    IFCI_TRY(st);
+    hs.resize(n);
+    IFCI_CUDA_TRY(h, cudaMemcpyAsync(hs.data(), b.d_state, n * sizeof(DavState), cudaMemcpyDeviceToHost, s));
+    if (blk) {
+        blk->assign((size_t)n * 2, 1e300);
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(blk->data(), b.d_blk_energy, (size_t)n * 2 * sizeof(double),
+                                         cudaMemcpyDeviceToHost, s));
+    }
+    IFCI_CUDA_TRY(h, cudaStreamSynchronize(s));
+    // lowest block of every sectored unit -> whole-space vector
+    if (b.any_sector) {
+        std::vector<double *> dst(n, nullptr);
+        bool any = false;
+        for (int u = 0; u < nu; u++) {
+            const Unit &U = units[u];
+            if (!U.sector || !U.expand_to) continue;
+            int best = U.prob0;
+            for (int i = U.prob0; i < U.prob0 + U.nprob; i++)
+                if (hs[i].energy < hs[best].energy) best = i;
+            dst[best] = U.expand_to;
+            const long long ndet = binom(U.spec.n, U.spec.m) * binom(U.spec.n, U.spec.m);
+            IFCI_CUDA_TRY(h, cudaMemsetAsync(U.expand_to, 0, (size_t)ndet * 8, s));
+            any = true;
+        }
+        if (any) {
+            IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.dst, dst.data(), n * sizeof(double *), cudaMemcpyHostToDevice, s));
+            IFCI_TRY(launch_sector_expand(h, b, mem.dst, s));
+            IFCI_CUDA_TRY(h, cudaStreamSynchronize(s));
+        }
+    }
+    return IFCI_OK;
 }
+
+}  // namespace
 
 int hi_precision_of(const ifci_davidson_opts_t &o) {
     if (o.precision == IFCI_FP64) return IFCI_FP64;
@@ -86,188 +432,227 @@ int check_opts(ifci_handle_t h, const ifci_davidson_opts_t &o) {
         return set_error(h, IFCI_ERR_INVALID_ARG, "davidson: max_space %d outside 3..%d", o.max_space, kMaxSpace);
     if (o.max_iter < 1) return set_error(h, IFCI_ERR_INVALID_ARG, "davidson: max_iter %d", o.max_iter);
     if (!(o.e_tol > 0) || !(o.r_tol > 0)) return set_error(h, IFCI_ERR_INVALID_ARG, "davidson: tolerances");
+    if (!(o.decouple_tol >= 0)) return set_error(h, IFCI_ERR_INVALID_ARG, "davidson: decouple_tol");
     return IFCI_OK;
 }
 
 int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o, double *energies,
               int *iters, int *status, cudaStream_t s, double *blk_energy) {
-    const int n = (int)specs.size();
-    if (n == 0) return IFCI_OK;
+    const int nspec = (int)specs.size();
+    if (nspec == 0) return IFCI_OK;
     IFCI_TRY(check_opts(h, o));
-    DavSizes z;
-    dav_layout(specs, o, z);
-    const bool lo = o.precision == IFCI_FP32 || o.precision == IFCI_TF32 || o.precision == IFCI_BF16;
-    const bool tc = o.precision == IFCI_BF16 || o.precision == IFCI_TF32;
-    const int hi_prec = hi_precision_of(o);
-    const bool oz = hi_prec == IFCI_FP64E;
-    const int ms = o.max_space;
+    DavArena arena(h);   // every piece below comes from the Davidson workspace
 
-    // string tables per class
-    std::map<std::pair<int, int>, std::pair<uint64_t *, int32_t *>> tables;
-    std::map<std::pair<int, int>, uint8_t *> blocks;
-    std::map<std::pair<int, int>, int32_t *> pmaps;
-    for (const ProbSpec &p : specs) {
-        auto key = std::make_pair(p.n, p.m);
-        if (tables.count(key)) continue;
-        int nstr = 0, nexc = 0;
-        if (ifci_string_counts(p.n, p.m, &nstr, &nexc) != IFCI_OK || p.m < 1)
-            return set_error(h, IFCI_ERR_INVALID_ARG, "davidson: problem with norb=%d nelec_spin=%d", p.n, p.m);
-        uint64_t *st = ws_take<uint64_t>(h, nstr);
-        int32_t *ex = ws_take<int32_t>(h, (size_t)nstr * nexc);
-        if (!st || !ex) return set_error(h, IFCI_ERR_OOM, "davidson: workspace (strings)");
-        IFCI_TRY(ifci_build_strings(h, p.n, p.m, st, ex, (ifci_stream_t)s));
-        tables[key] = {st, ex};
-        uint8_t *bl = ws_take<uint8_t>(h, (size_t)nstr * kBlk16Stride);
-        if (!bl) return set_error(h, IFCI_ERR_OOM, "davidson: workspace (block table)");
-        IFCI_TRY(launch_exc_blocks(h, nstr, nexc, ex, bl, s));
-        blocks[key] = bl;
-        // Davidson vectors are spin-flip symmetric: the tensor-core sigmas use
-        // the alpha-only gathers where the pair map's offsets fit in int32
-        int32_t *pm = nullptr;
-        if ((tc || oz) && 2ll * nstr * nstr < (1ll << 31)) {
-            const int np = p.n * (p.n + 1) / 2;
-            pm = ws_take<int32_t>(h, (size_t)nstr * pmap_ld(np));
-            if (!pm) return set_error(h, IFCI_ERR_OOM, "davidson: workspace (pair map)");
-            IFCI_TRY(launch_pair_map(h, nstr, nexc, np, ex, pm, s));
-        }
-        pmaps[key] = pm;
+    // ---- orbital groups of every problem (coupling graph above decouple_tol)
+    std::vector<std::vector<int>> label(nspec);
+    std::vector<int> ngroup(nspec, 1);
+    if (o.decouple_tol > 0) {
+        std::vector<CoupDesc> cd(nspec);
+        for (int i = 0; i < nspec; i++) cd[i] = CoupDesc{specs[i].n, specs[i].h1, specs[i].eri};
+        IFCI_TRY(ws_reserve(h, ws_round(nspec * sizeof(CoupDesc)) + ws_round((size_t)nspec * 32 * 4) + 1024));
+        auto *d_cd = ws_take<CoupDesc>(h, nspec);
+        auto *d_adj = ws_take<uint32_t>(h, (size_t)nspec * 32);
+        if (!d_cd || !d_adj) return set_error(h, IFCI_ERR_OOM, "davidson: workspace (coupling)");
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_cd, cd.data(), nspec * sizeof(CoupDesc), cudaMemcpyHostToDevice, s));
+        IFCI_TRY(launch_coupling(h, nspec, d_cd, o.decouple_tol, d_adj, s));
+        std::vector<uint32_t> adj((size_t)nspec * 32);
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(adj.data(), d_adj, adj.size() * 4, cudaMemcpyDeviceToHost, s));
+        IFCI_CUDA_TRY(h, cudaStreamSynchronize(s));
+        for (int i = 0; i < nspec; i++) orbital_groups(adj.data() + (size_t)i * 32, specs[i].n, label[i], ngroup[i]);
     }
 
-    DavBatch b;
-    b.nprob = n;
-    b.max_space = ms;
-    b.keep = std::min(kKeep, ms - 2);
-    b.precision = o.precision;
-    b.hi_precision = hi_prec;
-    b.max_iter = o.max_iter;
-    b.graph_iters = o.graph_iters > 0 ? o.graph_iters : 0;
-    b.e_tol = o.e_tol;
-    b.r_tol = o.r_tol;
-    SigmaPlan hi, lop;
-    std::vector<FoldDesc> folds(n);
-    std::vector<HdiagDesc> hds(n);
-    std::vector<int> hw_prob;
-    std::vector<long long> hw_start;
-    for (int i = 0; i < n; i++) {
+    // ---- blocks of the sectored problems
+    std::vector<Unit> units;
+    std::vector<BlockSpec> blocks;
+    std::vector<int> sidx;
+    std::vector<int> sectored;   // spec indices with more than one group
+    for (int i = 0; i < nspec; i++) {
         const ProbSpec &p = specs[i];
-        auto tb = tables[{p.n, p.m}];
-        int nstr = (int)binom(p.n, p.m), nexc = p.m * (p.n - p.m + 1);
-        long long ndet = (long long)nstr * nstr;
-        int np = p.n * (p.n + 1) / 2;
-        double *W = ws_take<double>(h, (size_t)np * np);
-        float *Wf = lo ? ws_take<float>(h, (size_t)np * np) : nullptr;
-        void *Wtc = tc ? (void *)ws_take<char>(h, tc_operand_bytes(np, o.precision)) : nullptr;
-        char *Woz = oz ? ws_take<char>(h, oz_operand_bytes(np)) : nullptr;
-        double *hd = ws_take<double>(h, ndet);
-        double *B = ws_take<double>(h, (size_t)(ms + 1) * ndet);
-        double *S = ws_take<double>(h, (size_t)(ms + 1) * ndet);
-        if (!W || !hd || !B || !S || (lo && !Wf) || (tc && !Wtc) || (oz && !Woz))
-            return set_error(h, IFCI_ERR_OOM, "davidson: workspace (problem %d)", i);
-        folds[i] = FoldDesc{p.n, 2 * p.m, np, p.h1, p.eri, W};
-        hds[i] = HdiagDesc{p.n, nstr, tb.first, p.h1, p.eri, hd};
-        for (long long s0 = 0; s0 < ndet; s0 += kVecChunk) {
-            hw_prob.push_back(i);
-            hw_start.push_back(s0);
+        const int nstr = (int)binom(p.n, p.m);
+        Unit U{p, p.h1, p.eri, false, nullptr, (int)blocks.size(), 1, nullptr};
+        if (ngroup[i] > 1 && ngroup[i] <= 16 && p.m >= 1) {
+            // class of a string = electrons per group, 4 bits per group
+            std::vector<uint32_t> gmask(ngroup[i], 0u);
+            for (int q = 0; q < p.n; q++) gmask[label[i][q]] |= 1u << q;
+            const std::vector<uint32_t> strs = host_strings(p.n, p.m);
+            std::unordered_map<uint64_t, int> cid;
+            std::vector<std::vector<int>> members;
+            for (int si = 0; si < nstr; si++) {
+                uint64_t key = 0;
+                for (int g = 0; g < ngroup[i]; g++) key |= (uint64_t)__builtin_popcount(strs[si] & gmask[g]) << (4 * g);
+                auto it = cid.find(key);
+                if (it == cid.end()) {
+                    it = cid.emplace(key, (int)members.size()).first;
+                    members.emplace_back();
+                }
+                members[it->second].push_back(si);
+            }
+            if (members.size() > 1) {
+                std::vector<int> off(members.size());
+                for (size_t a = 0; a < members.size(); a++) {
+                    off[a] = (int)sidx.size();
+                    sidx.insert(sidx.end(), members[a].begin(), members[a].end());
+                }
+                U.sector = true;
+                U.nprob = 0;
+                for (size_t a = 0; a < members.size(); a++)
+                    for (size_t c = a; c < members.size(); c++) {
+                        BlockSpec bs{};
+                        bs.unit = (int)units.size();
+                        bs.na = (int)members[a].size();
+                        bs.nb = (int)members[c].size();
+                        bs.sym = a == c;
+                        bs.sa_off = off[a];
+                        bs.sb_off = off[c];
+                        bs.ndet = (long long)bs.na * bs.nb;
+                        bs.ndim = bs.sym ? (long long)bs.na * (bs.na + 1) / 2 : bs.ndet;
+                        blocks.push_back(bs);
+                        U.nprob++;
+                    }
+                sectored.push_back(i);
+            }
         }
-        DavProb dp{};
-        dp.ndet = ndet;
-        dp.nstr = nstr;
-        dp.item0 = (int)b.vitems.size();
-        for (long long s0 = 0; s0 < ndet; s0 += kVecChunk) b.vitems.push_back(WorkItem{i, 0, s0});
-        dp.nitem = (int)b.vitems.size() - dp.item0;
-        dp.B = B;
-        dp.S = S;
-        dp.hd = hd;
-        dp.c_out = p.c_out;
-        dp.e_core = p.e_core;
-        dp.seed_block = p.seed_block;
-        b.probs.push_back(dp);
-        SigmaProb sp{};
-        sp.n = p.n; sp.nstr = nstr; sp.nexc = nexc; sp.np = np; sp.ld = np;
-        sp.ndet = ndet; sp.stride = ndet; sp.exc = tb.second;
-        sp.blk = blocks[{p.n, p.m}];
-        sp.pmap = pmaps[{p.n, p.m}];
-        sp.sym = sp.pmap ? 1 : 0;   // plan_sigma keeps it for the tensor-core plans only
-        sp.W = W; sp.Wf = Wf; sp.Wtc = Wtc;
-        sp.Woz = Woz;
-        sp.Wexp = oz ? (double *)(Woz + (oz_operand_bytes(np) - np * 8 - 256)) : nullptr;
-        sp.dscale = 2.0;   // basis vectors are normalised: |D| <= 2
-        sp.cbase = B; sp.sbase = S;
-        hi.probs.push_back(sp);
-        lop.probs.push_back(sp);
+        if (!U.sector) {
+            BlockSpec bs{};
+            bs.unit = (int)units.size();
+            bs.na = bs.nb = nstr;
+            bs.sym = 1;
+            bs.sa_off = bs.sb_off = -1;
+            bs.ndet = (long long)nstr * nstr;
+            bs.ndim = (long long)nstr * (nstr + 1) / 2;
+            blocks.push_back(bs);
+        }
+        units.push_back(U);
     }
-    b.d_probs = ws_take<DavProb>(h, n);
-    b.d_state = ws_take<DavState>(h, n);
-    b.d_vitems = ws_take<WorkItem>(h, b.vitems.size());
-    b.d_part = ws_take<double>(h, b.vitems.size() * kNP);
-    b.d_gs = ws_take<double>(h, (size_t)n * kMaxSpace * kMaxSpace);
-    b.d_y = ws_take<double>(h, (size_t)n * kYStride);
-    b.d_coef = ws_take<double>(h, (size_t)n * kNP);
-    b.d_nactive = ws_take<int>(h, 2);
-    b.d_blk_energy = ws_take<double>(h, (size_t)n * 2);
-    int *d_hi = ws_take<int>(h, n), *d_lo = ws_take<int>(h, n);
-    auto *d_fold = ws_take<FoldDesc>(h, n);
-    auto *d_hd = ws_take<HdiagDesc>(h, n);
-    int *d_hwp = ws_take<int>(h, hw_prob.size());
-    long long *d_hws = ws_take<long long>(h, hw_start.size());
-    void *D = ws_take<char>(h, (size_t)z.budget * 8);
-    void *G = ws_take<char>(h, (size_t)z.budget * 8);
-    if (!b.d_probs || !b.d_state || !b.d_vitems || !b.d_part || !b.d_gs || !b.d_y || !b.d_coef || !b.d_nactive ||
-        !d_hi || !d_lo || !d_fold || !d_hd || !d_hwp || !d_hws || !D || !G)
-        return set_error(h, IFCI_ERR_OOM, "davidson: workspace (batch)");
-    // sigma selection flags: hi plan for FP64 sigma, lo plan for the bulk precision
-    for (int i = 0; i < n; i++) {
-        hi.probs[i].cslot = &b.d_state[i].newest;
-        hi.probs[i].sslot = &b.d_state[i].newest;
-        hi.probs[i].active = d_hi + i;
-        lop.probs[i].cslot = &b.d_state[i].newest;
-        lop.probs[i].sslot = &b.d_state[i].newest;
-        lop.probs[i].active = d_lo + i;
-    }
-    IFCI_TRY(plan_sigma(h, hi, z.budget, hi_prec));
-    if (lo) {
-        long long budget_lo = z.budget * 8 / (long long)sigma_elem_bytes(o.precision);
-        IFCI_TRY(plan_sigma(h, lop, budget_lo, o.precision));
-    }
-    IFCI_TRY(upload_plan(h, hi, s));
-    if (lo) IFCI_TRY(upload_plan(h, lop, s));
 
-    IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_fold, folds.data(), n * sizeof(FoldDesc), cudaMemcpyHostToDevice, s));
-    IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_hd, hds.data(), n * sizeof(HdiagDesc), cudaMemcpyHostToDevice, s));
-    IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_hwp, hw_prob.data(), hw_prob.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-    IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_hws, hw_start.data(), hw_start.size() * sizeof(long long),
-                                     cudaMemcpyHostToDevice, s));
-    IFCI_CUDA_TRY(h, cudaMemcpyAsync(b.d_probs, b.probs.data(), n * sizeof(DavProb), cudaMemcpyHostToDevice, s));
-    IFCI_CUDA_TRY(h, cudaMemcpyAsync(b.d_vitems, b.vitems.data(), b.vitems.size() * sizeof(WorkItem),
-                                     cudaMemcpyHostToDevice, s));
-    IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_gs, 0, (size_t)n * kMaxSpace * kMaxSpace * 8, s));
-    IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_y, 0, (size_t)n * kYStride * 8, s));
-    int maxnp = 0;
-    for (const ProbSpec &p : specs) maxnp = std::max(maxnp, p.n * (p.n + 1) / 2);
-    IFCI_TRY(launch_fold(h, n, d_fold, maxnp, s));
-    if (lo) IFCI_TRY(launch_convert_w(h, n, lop.d_probs, s));
-    if (tc) IFCI_TRY(launch_tc_pack_w(h, n, lop.d_probs, o.precision, s));
-    if (oz) IFCI_TRY(launch_oz_pack_w(h, n, hi.d_probs, s));
-    IFCI_TRY(launch_hdiag(h, d_hd, d_hwp, d_hws, (int)hw_prob.size(), kVecChunk, s));
-    IFCI_TRY(dav_init(h, b, d_hd, s));
+    // ---- H' of the sectored problems and the whole-space start vectors of the polish
+    double *scratch = nullptr;   // [masked h1, masked eri] per sectored problem, then seeds
+    std::vector<double *> seeds(nspec, nullptr);
+    std::vector<int> polished;   // sectored problems whose dropped integrals are not negligible
+    if (!sectored.empty()) {
+        size_t bytes = 0;
+        for (int i : sectored) {
+            const long long np = specs[i].n * (specs[i].n + 1) / 2, nstr = binom(specs[i].n, specs[i].m);
+            bytes += ws_round((size_t)specs[i].n * specs[i].n * 8) + ws_round((size_t)np * np * 8);
+            if (!specs[i].c_out) bytes += ws_round((size_t)nstr * nstr * 8);
+        }
+        bytes += ws_round(sectored.size() * sizeof(double));
+        IFCI_CUDA_TRY(h, cudaMalloc(&scratch, bytes + ws_round(sectored.size() * sizeof(MaskDesc))));
+        char *q = reinterpret_cast<char *>(scratch);
+        double *d_dropped = reinterpret_cast<double *>(q);
+        q += ws_round(sectored.size() * sizeof(double));
+        std::vector<MaskDesc> md;
+        for (int i : sectored) {
+            const long long np = specs[i].n * (specs[i].n + 1) / 2, nstr = binom(specs[i].n, specs[i].m);
+            MaskDesc d{};
+            d.n = specs[i].n;
+            d.h1 = specs[i].h1;
+            d.eri = specs[i].eri;
+            d.h1m = reinterpret_cast<double *>(q);
+            q += ws_round((size_t)specs[i].n * specs[i].n * 8);
+            d.erim = reinterpret_cast<double *>(q);
+            q += ws_round((size_t)np * np * 8);
+            for (int p = 0; p < 32; p++) d.label[p] = p < specs[i].n ? (unsigned char)label[i][p] : 0;
+            d.dropped = d_dropped + md.size();
+            if (specs[i].c_out) {
+                seeds[i] = specs[i].c_out;   // the polish copies its start vector before it writes c_out
+            } else {
+                seeds[i] = reinterpret_cast<double *>(q);
+                q += ws_round((size_t)nstr * nstr * 8);
+            }
+            units[i].h1 = d.h1m;
+            units[i].eri = d.erim;
+            md.push_back(d);
+        }
+        auto *d_md = reinterpret_cast<MaskDesc *>(q);
+        std::vector<double> dropped(sectored.size(), 0.0);
+        int rc = IFCI_OK;
+        if (cudaMemcpyAsync(d_md, md.data(), md.size() * sizeof(MaskDesc), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            rc = set_error(h, IFCI_ERR_CUDA, "davidson: mask descriptors");
+        if (rc == IFCI_OK) rc = launch_mask(h, (int)md.size(), d_md, s);
+        if (rc == IFCI_OK && (cudaMemcpyAsync(dropped.data(), d_dropped, dropped.size() * 8, cudaMemcpyDeviceToHost,
+                                              s) != cudaSuccess ||
+                              cudaStreamSynchronize(s) != cudaSuccess))
+            rc = set_error(h, IFCI_ERR_CUDA, "davidson: dropped integrals");
+        if (rc != IFCI_OK) {
+            cudaStreamSynchronize(s);
+            cudaFree(scratch);
+            return rc;
+        }
+        // H - H' below kPolishTol everywhere: the lowest block's eigenpair is the
+        // eigenpair of H to far below any tolerance (second order in H - H'), and
+        // its vector is the result; otherwise the polish refines it with the full H
+        for (size_t k = 0; k < sectored.size(); k++) {
+            const int i = sectored[k];
+            if (dropped[k] > kPolishTol) {
+                polished.push_back(i);
+                units[i].expand_to = seeds[i];
+            } else if (specs[i].c_out) {
+                units[i].expand_to = specs[i].c_out;
+            }
+        }
+    }
 
-    int *h_nactive = nullptr;
-    IFCI_CUDA_TRY(h, cudaMallocHost(&h_nactive, 2 * sizeof(int)));
-    int st = dav_iterate(h, b, hi, lo ? &lop : nullptr, d_hi, d_lo, D, G, h_nactive, s);
-    cudaFreeHost(h_nactive);
-    IFCI_TRY(st);
-    std::vector<DavState> hs(n);
-    IFCI_CUDA_TRY(h, cudaMemcpyAsync(hs.data(), b.d_state, n * sizeof(DavState), cudaMemcpyDeviceToHost, s));
-    if (blk_energy)
-        IFCI_CUDA_TRY(h, cudaMemcpyAsync(blk_energy, b.d_blk_energy, (size_t)n * 2 * sizeof(double),
-                                         cudaMemcpyDeviceToHost, s));
-    IFCI_CUDA_TRY(h, cudaStreamSynchronize(s));
+    // ---- the run over every unit; then the polish of the sectored ones
+    std::vector<DavState> hs;
+    std::vector<double> blk;
+    int rc = dav_run(h, units, blocks, sidx, o, s, hs, blk_energy ? &blk : nullptr);
+    std::vector<DavState> hp;
+    if (rc == IFCI_OK && !polished.empty()) {
+        std::vector<Unit> pu;
+        std::vector<BlockSpec> pb;
+        for (int i : polished) {
+            const ProbSpec &p = specs[i];
+            const int nstr = (int)binom(p.n, p.m);
+            Unit U{p, p.h1, p.eri, false, seeds[i], (int)pb.size(), 1, nullptr};
+            U.spec.seed_block = 0;
+            BlockSpec bs{};
+            bs.unit = (int)pu.size();
+            bs.na = bs.nb = nstr;
+            bs.sym = 1;
+            bs.sa_off = bs.sb_off = -1;
+            bs.ndet = (long long)nstr * nstr;
+            bs.ndim = (long long)nstr * (nstr + 1) / 2;
+            pb.push_back(bs);
+            pu.push_back(U);
+        }
+        ifci_davidson_opts_t op = o;
+        op.sector_passes = 0;
+        rc = dav_run(h, pu, pb, std::vector<int>(), op, s, hp, nullptr);
+    }
+    if (scratch) {
+        cudaStreamSynchronize(s);
+        cudaFree(scratch);
+    }
+    IFCI_TRY(rc);
+
+    // ---- per problem: the lowest block (then its polish) for sectored problems
     int ret = IFCI_OK;
-    for (int i = 0; i < n; i++) {
-        if (energies) energies[i] = hs[i].energy;
-        if (iters) iters[i] = hs[i].iters;
-        if (status) status[i] = hs[i].status;
-        if (hs[i].status != IFCI_OK) ret = IFCI_ERR_NOT_CONVERGED;
+    std::vector<int> polish_of(nspec, -1);
+    for (size_t k = 0; k < polished.size(); k++) polish_of[polished[k]] = (int)k;
+    for (int i = 0; i < nspec; i++) {
+        const Unit &U = units[i];
+        int best = U.prob0, it = 0, stt = IFCI_OK;
+        for (int j = U.prob0; j < U.prob0 + U.nprob; j++) {
+            if (hs[j].energy < hs[best].energy) best = j;
+            it = std::max(it, hs[j].iters);
+            if (hs[j].status != IFCI_OK) stt = hs[j].status;
+        }
+        double e = hs[best].energy;
+        if (polish_of[i] >= 0) {
+            const DavState &q = hp[polish_of[i]];
+            e = q.energy;
+            it += q.iters;
+            if (q.status != IFCI_OK) stt = q.status;
+        }
+        if (energies) energies[i] = e;
+        if (iters) iters[i] = it;
+        if (status) status[i] = stt;
+        if (blk_energy) {
+            blk_energy[2 * i] = blk[2 * best];
+            blk_energy[2 * i + 1] = blk[2 * best + 1];
+        }
+        if (stt != IFCI_OK) ret = IFCI_ERR_NOT_CONVERGED;
     }
     if (ret != IFCI_OK) set_error(h, ret, "davidson: some problems did not converge");
     return ret;
@@ -277,7 +662,6 @@ int dav_solve_sectors(ifci_handle_t h, const std::vector<ProbSpec> &specs, const
                       double *energies, int *iters, int *status, cudaStream_t s) {
     const int n = (int)specs.size();
     if (o.sector_passes < 2 || n == 0) return dav_solve(h, specs, o, energies, iters, status, s);
-    const size_t mark = h->ws_top;
     std::vector<int> st_local;
     if (!status) {   // the merge needs every problem's status
         st_local.assign(n, IFCI_OK);
@@ -307,7 +691,6 @@ int dav_solve_sectors(ifci_handle_t h, const std::vector<ProbSpec> &specs, const
         if (again[k].c_out) again[k].c_out = reinterpret_cast<double *>(reinterpret_cast<char *>(tmp) + voff[k]);
     std::vector<double> e2(again.size());
     std::vector<int> it2(again.size()), st2(again.size());
-    h->ws_top = mark;
     const int r2 = dav_solve(h, again, o, e2.data(), it2.data(), st2.data(), s);
     int ret = IFCI_OK;
     if (r2 == IFCI_OK || r2 == IFCI_ERR_NOT_CONVERGED) {
@@ -355,6 +738,7 @@ void ifci_davidson_default_opts(ifci_davidson_opts_t *o) {
     o->det_budget = 0;
     o->graph_iters = 0;
     o->sector_passes = 0;
+    o->decouple_tol = 1e-5;
 }
 
 int ifci_davidson_batched(ifci_handle_t h, int nprob, const ifci_problem_t *probs, const ifci_davidson_opts_t *opts,
@@ -375,7 +759,6 @@ int ifci_davidson_batched(ifci_handle_t h, int nprob, const ifci_problem_t *prob
     }
     IFCI_TRY(check_opts(h, o));
     IFCI_CUDA_TRY(h, cudaSetDevice(h->device));
-    IFCI_TRY(ws_reserve(h, dav_workspace_bytes(specs, o)));
     return dav_solve_sectors(h, specs, o, energies, iters, status, as_cuda(stream));
 }
 

@@ -15,25 +15,29 @@ struct ProbSpec {
                             // r-th lowest decoupled block of the P-space matrix
 };
 
-struct DavSizes {
-    size_t bytes = 0;
-    int nitem = 0, nclass = 0;
-    long long max_pd = 0, sum_pd = 0, budget = 0;
-    long long n_items_sigma = 0, n_tiles_sigma = 0;
+// coupling graph of one problem's orbitals (sectors.cu)
+struct CoupDesc {
+    int n;
+    const double *h1, *eri;
+};
+// H' of a sectored problem: h1, eri with every integral that joins two groups set to zero
+struct MaskDesc {
+    int n;
+    const double *h1, *eri;
+    double *h1m, *erim;
+    double *dropped;           // out: largest |integral| set to zero
+    unsigned char label[32];   // group of each orbital
 };
 
 int check_opts(ifci_handle_t h, const ifci_davidson_opts_t &o);
 int hi_precision_of(const ifci_davidson_opts_t &o);   // precision of the exact (restart) sigma
-// Upper bound of the workspace dav_solve takes (with ws_take) for these problems.
-size_t dav_workspace_bytes(const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o);
-// Solves every problem; carves its memory from the handle workspace after
-// whatever the caller already took.  Outputs are host arrays (may be null
-// except energies).  Synchronous.
+// Solves every problem; its memory comes from the handle's Davidson workspace
+// (DavArena), sized here.  Outputs are host arrays (may be null except
+// energies).  Synchronous.
 int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o, double *energies,
               int *iters, int *status, cudaStream_t s, double *blk_energy = nullptr);
 // dav_solve, then (opts.sector_passes >= 2) a second pass over the problems
-// whose P-space shows a competitive second block; the workspace above `mark`
-// is reused by the second pass.
+// whose P-space shows a competitive second block.
 int dav_solve_sectors(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o,
                       double *energies, int *iters, int *status, cudaStream_t s);
 int dav_init(ifci_handle_t h, DavBatch &b, const HdiagDesc *d_hd, cudaStream_t s);
@@ -41,5 +45,15 @@ size_t psp_workspace_bytes(int nprob);
 int launch_pspace_start(ifci_handle_t h, const DavBatch &b, const HdiagDesc *d_hd, cudaStream_t s);
 int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_plan, int *d_hi, int *d_lo,
                 void *D, void *G, int *h_nactive, cudaStream_t s);
+
+// sectors.cu
+int launch_coupling(ifci_handle_t h, int nprob, const CoupDesc *d_desc, double tau, uint32_t *d_adj, cudaStream_t s);
+int launch_mask(ifci_handle_t h, int nprob, const MaskDesc *d_desc, cudaStream_t s);
+int launch_sector_gather(ifci_handle_t h, const DavBatch &b, const int *flag, cudaStream_t s);
+int launch_sector_scatter(ifci_handle_t h, const DavBatch &b, const int *flag, cudaStream_t s);
+int launch_sector_hd(ifci_handle_t h, const DavBatch &b, cudaStream_t s);
+int launch_unit_flags(ifci_handle_t h, const DavBatch &b, const int *hi, const int *lo, cudaStream_t s);
+int launch_sector_expand(ifci_handle_t h, const DavBatch &b, double *const *d_dst, cudaStream_t s);
+void orbital_groups(const uint32_t *adj, int n, std::vector<int> &label, int &ngroup);
 
 }  // namespace ifci

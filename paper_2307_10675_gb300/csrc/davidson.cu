@@ -111,7 +111,7 @@ __global__ void init_kernel(const DavProb *__restrict__ probs, DavState *__restr
         s.tnorm2 = 0.0;
         s.energy = 0.0;
         int nv, ns;
-        start_block(p.nstr, max_space, &nv, &ns);
+        start_block(p.ndim, max_space, p.seed != nullptr, &nv, &ns);
         s.noise_slot = ns;
         s.tgt = 0;
         for (int r = 0; r < kKeep; r++) s.rn[r] = 1e300;
@@ -131,21 +131,26 @@ __device__ __forceinline__ double pair_noise(int a, int b) {
 }
 
 // Start block: the P-space slots 0..nv-1 zeroed (pspace.cu fills them), the
-// random symmetric vector in the noise slot (normalised after pspace.cu has
-// cleared it on the P-space determinants).
+// random vector in the noise slot (normalised after pspace.cu has cleared it
+// on the P-space determinants; a function of the global string pair, so it is
+// symmetric in a symmetric block).  A problem with a start vector of its own
+// copies it to slot 0.
 __global__ void __launch_bounds__(256) init_vec_kernel(const DavProb *__restrict__ probs,
                                                        const WorkItem *__restrict__ items, int max_space) {
     const WorkItem it = items[blockIdx.x];
     const DavProb &p = probs[it.prob];
-    const int n = p.nstr;
     int nv, ns;
-    start_block(n, max_space, &nv, &ns);
+    start_block(p.ndim, max_space, p.seed != nullptr, &nv, &ns);
     long long end = min(it.start + (long long)kVecChunk, p.ndet);
     for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) {
+        if (p.seed) {
+            p.B[I] = p.seed[I];
+            continue;
+        }
         for (int r = 0; r < nv; r++) p.B[(long long)r * p.ndet + I] = 0.0;
         if (ns >= 0) {
-            const int a = (int)(I / n), b = (int)(I % n);
-            p.B[(long long)ns * p.ndet + I] = pair_noise(a, b);
+            const int a = (int)(I / p.nb), b = (int)(I % p.nb);
+            p.B[(long long)ns * p.ndet + I] = pair_noise(blk_row(p, a), blk_col(p, b));
         }
     }
 }
@@ -401,10 +406,13 @@ __global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__rest
         }
         s.rebuild_to = 0;   // every basis vector has its exact sigma: a normal iteration
     }
-    // a competitive higher root: within kCompete of the lowest and not yet resolved
+    // a competitive higher root: within kCompete of the lowest and not yet
+    // resolved.  A problem started from a vector of its own refines that root
+    // only (its sector was chosen before), and so does a block of a sectored
+    // space: the search over its decoupled sectors is the set of blocks
     const double tol2 = fmax(sqrt(r_tol), 10.0 * r_tol);
     int comp = -1;
-    for (int r = 1; r < nk && comp < 0; r++)
+    for (int r = 1; r < nk && comp < 0 && !p.seed && !p.gc; r++)
         if (ys_i[r * kNP + kMaxSpace] - ys_i[kMaxSpace] < kCompete && s.rn[r] > tol2) comp = r;
     // only exact sigmas decide convergence: the lowest root's residual below
     // r_tol, a settled energy, and no competitive root left unresolved
@@ -432,8 +440,8 @@ __global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__rest
     atomicAdd(nactive, 1);
     double *c = coef + (long long)i * kNP;
     double *Gm = gs + (long long)i * kMaxSpace * kMaxSpace;
-    // the spin-flip-even sector has nstr (nstr + 1) / 2 dimensions
-    const int nsym = p.nstr * (p.nstr + 1) / 2;
+    // dimension of the space iterated (the spin-flip-even sector of a symmetric block)
+    const long long nsym = p.ndim;
     const int ra = lowmix ? restart_at : max_space;
     if (k >= ra || k >= nsym || s.force) {
         const bool exhausted = k >= nsym || s.force;
@@ -605,8 +613,9 @@ __global__ void reduce_coef_kernel(const DavProb *__restrict__ probs, DavState *
     if (threadIdx.x > k && threadIdx.x < kMaxSpace) coef[(long long)i * kNP + threadIdx.x] = 0.0;
 }
 
-// b_k = t / |t|, symmetrised over (I_a, I_b) <-> (I_b, I_a); the new slot becomes
-// the next sigma target.  One thread per pair (I, I^T) with I_a >= I_b.
+// b_k = t / |t|, symmetrised over (I_a, I_b) <-> (I_b, I_a) in a symmetric
+// block; the new slot becomes the next sigma target.  One thread per pair
+// (I, I^T) with I_a >= I_b (per element in an off-diagonal block).
 __global__ void __launch_bounds__(256) normalize_kernel(const DavProb *__restrict__ probs,
                                                         const DavState *__restrict__ st,
                                                         const WorkItem *__restrict__ items, int max_space) {
@@ -622,7 +631,11 @@ __global__ void __launch_bounds__(256) normalize_kernel(const DavProb *__restric
         dst = p.B + (long long)s.k * p.ndet;
     }
     long long end = min(it.start + (long long)kVecChunk, p.ndet);
-    const int n = p.nstr;
+    if (!p.sym) {
+        for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) dst[I] = T[I] * inv;
+        return;
+    }
+    const int n = p.nb;
     for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) {
         int a = (int)(I / n), b = (int)(I % n);
         if (a < b) continue;
@@ -722,8 +735,22 @@ static int dav_step(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan 
     const int restart_at = b.max_space;
     select_kernel<<<(b.nprob + 127) / 128, 128, 0, s>>>(b.d_state, b.nprob, mixed ? 1 : 0, d_hi, d_lo);
     IFCI_LAUNCH_CHECK(h);
+    IFCI_TRY(launch_unit_flags(h, b, d_hi, d_lo, s));
+    // blocks of a sectored space: their newest vectors form one whole-space
+    // input, whose sigma each block takes its part of
+    auto sector_move = [&](bool in, const int *flag) -> int {
+        if (!b.any_sector) return IFCI_OK;
+        ProfScope ps(h, s, PK_OTHER);
+        return in ? launch_sector_gather(h, b, flag, s) : launch_sector_scatter(h, b, flag, s);
+    };
+    IFCI_TRY(sector_move(true, d_hi));
     IFCI_TRY(run_sigma(h, hi_plan, b.hi_precision, D, G, s));
-    if (mixed) IFCI_TRY(run_sigma(h, *lo_plan, b.precision, D, G, s));
+    IFCI_TRY(sector_move(false, d_hi));
+    if (mixed) {
+        IFCI_TRY(sector_move(true, d_lo));
+        IFCI_TRY(run_sigma(h, *lo_plan, b.precision, D, G, s));
+        IFCI_TRY(sector_move(false, d_lo));
+    }
     ProfScope vec_scope(h, s, PK_VECTOR);
     dots_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);
     IFCI_LAUNCH_CHECK(h);

@@ -4,17 +4,34 @@
 
 namespace ifci {
 
+// A Davidson problem iterates in a rectangular block of a CI space: rows are
+// alpha strings sa[0..na), columns beta strings sb[0..nb) (nullptr: every
+// string, in order), vector index I = ia * nb + ib.  A whole CI space is the
+// block with na = nb = nstr.  sym = 1: the block is its own spin-flip image
+// (sa == sb) and its vectors are kept symmetric, x[ia][ib] = x[ib][ia]; the
+// space iterated is then the na (na + 1) / 2 symmetric vectors.  sym = 0: an
+// off-diagonal block (alpha and beta classes differ) whose spin-flip image
+// is not stored; every vector of the block counts (ndim = na * nb).
 struct DavProb {
-    long long ndet;
-    int nstr;
+    long long ndet;          // na * nb
+    long long ndim;          // dimension of the vector space iterated (see above)
+    int nstr;                // strings of the whole CI space
+    int na, nb, sym;
     int item0, nitem;        // range of vector work items
     int seed_block;          // 0: default start block; r >= 1: from the r-th P-space block (second pass)
+    const int *sa, *sb;      // global string index of each row / column, or nullptr
     double *B;               // (max_space + 1) slots of ndet: basis vectors
     double *S;               // (max_space + 1) slots of ndet: sigma of each slot
     const double *hd;        // diagonal <I|H|I> (no constant)
     double *c_out;           // converged vector or nullptr
+    const double *seed;      // start vector (ndet, normalised) instead of the start block, or nullptr
+    double *gc, *gs;         // sector blocks: the whole space's sigma input / output (nstr^2) or nullptr
     double e_core;
 };
+
+// global string index of row / column r of a block
+__host__ __device__ inline int blk_row(const DavProb &p, int r) { return p.sa ? p.sa[r] : r; }
+__host__ __device__ inline int blk_col(const DavProb &p, int c) { return p.sb ? p.sb[c] : c; }
 
 struct DavState {
     int k;                   // basis vectors held (slots 0..k-1)
@@ -62,10 +79,19 @@ constexpr int kYStride = kKeep * kNP;
 constexpr int kStartP = 3;
 constexpr int kPspMax = 64;
 constexpr double kSectorWindow = 0.3;   // a second P-space block this close (Eh) gets its own pass
+// a sectored problem whose dropped integrals (H - H') are all below this
+// needs no polish with the full H: the energy changes at second order, ~1e-24
+constexpr double kPolishTol = 1e-12;
 
-// start block layout of a problem with nstr strings and subspace max_space
-__host__ __device__ inline void start_block(int nstr, int max_space, int *nv, int *noise_slot) {
-    const long long nsym = (long long)nstr * (nstr + 1) / 2;
+// start block layout of a problem iterating in ndim dimensions with subspace
+// max_space; a problem with a start vector of its own starts from that alone
+__host__ __device__ inline void start_block(long long ndim, int max_space, bool seeded, int *nv, int *noise_slot) {
+    if (seeded) {
+        *nv = 1;
+        *noise_slot = -1;
+        return;
+    }
+    const long long nsym = ndim;
     const bool noise = nsym > kPspMax && max_space >= 4;
     long long v = kStartP;
     if (v > nsym) v = nsym;
@@ -94,6 +120,13 @@ struct DavBatch {
     double *d_y = nullptr;        // [nprob][kYStride] lowest Ritz vectors and values
     double *d_coef = nullptr;     // [nprob][kNP]
     int *d_nactive = nullptr;
+    // sigma units (one CI space each; a sectored space has several problems)
+    int nunit = 0;
+    bool any_sector = false;
+    int2 *d_urange = nullptr;     // [nunit] first problem, problem count
+    long long *d_pidx = nullptr;  // [nprob][kPspMax] P-space determinants of the start block
+    int *d_pcount = nullptr;      // [nprob]
+    int *d_uhi = nullptr, *d_ulo = nullptr;   // [nunit] sigma flags of the hi / lo plan
 };
 
 

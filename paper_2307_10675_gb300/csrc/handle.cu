@@ -144,6 +144,7 @@ int ifci_handle_destroy(ifci_handle_t h) {
     ifci::prof_collect(h);
     for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
     if (h->ws) cudaFree(h->ws);
+    if (h->ws_alt) cudaFree(h->ws_alt);
     if (h->kept.vec) cudaFree(h->kept.vec);
     if (h->d_err) cudaFree(h->d_err);
     if (h->d_counter) cudaFree(h->d_counter);
@@ -154,7 +155,7 @@ int ifci_handle_destroy(ifci_handle_t h) {
 
 const char *ifci_last_error_string(ifci_handle_t h) { return h ? h->last_error.c_str() : "null handle"; }
 
-size_t ifci_workspace_bytes(ifci_handle_t h) { return h ? h->ws_bytes : 0; }
+size_t ifci_workspace_bytes(ifci_handle_t h) { return h ? h->ws_bytes + h->ws_alt_bytes : 0; }
 
 long long ifci_kernel_launches(ifci_handle_t h) { return h ? h->launches : 0; }
 

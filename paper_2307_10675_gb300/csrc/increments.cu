@@ -23,6 +23,27 @@ __global__ void increments_kernel(int nsub, const long long *__restrict__ sub_of
     eps[X] = v;
 }
 
+// Under screening, Eqs. 2-5 taken recursively for the sets x0..x1-1 (one
+// size): eps_X = E_c(X) - sum over the proper subsets Y of eps_Y, a screened
+// set's increment being 0 (its subsets' increments are already final).
+__global__ void increments_rec_kernel(int x0, int x1, const long long *__restrict__ sub_off,
+                                      const int *__restrict__ sub_idx, const char *__restrict__ incl,
+                                      const double *__restrict__ ex, const double *__restrict__ e0,
+                                      double *__restrict__ eps) {
+    const int X = x0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (X >= x1) return;
+    if (!incl[X]) {
+        eps[X] = 0.0;
+        return;
+    }
+    double v = ex[X] - *e0;
+    for (long long t = sub_off[X]; t < sub_off[X + 1]; t++) {
+        const int y = sub_idx[t];
+        if (y != X) v -= eps[y];
+    }
+    eps[X] = v;
+}
+
 // E_total = E_0 + sum_X eps_X, compensated summation in a fixed order.
 __global__ void total_kernel(int nsub, const double *__restrict__ eps, const double *__restrict__ e0,
                              double *__restrict__ total) {
@@ -101,7 +122,7 @@ int ifci_increments(ifci_handle_t h, const ifci_system_t *sys, int max_order, co
     // workspace: system copy, frozen-core outputs, subset tables, then Davidson batches
     size_t fixed = ws_round(ns * sizeof(FrozenDesc)) + ws_round(P.orbs.size() * 4) + ws_round((size_t)ns * 8) * 3 +
                    ws_round(8) * 2 + ws_round((ns + 1) * 8) + ws_round(P.sub_idx.size() * 4) +
-                   ws_round(P.sub_sgn.size()) + ws_round(sys->nbody * 4);
+                   ws_round(P.sub_sgn.size()) + ws_round(sys->nbody * 4) + ws_round(ns);
     if (sys->on_host) fixed += ws_round((size_t)norb * norb * 8) + ws_round((size_t)npg * npg * 8);
     std::vector<long long> h1_off(ns + 1, 0), eri_off(ns + 1, 0);
     for (int x = 0; x < ns; x++) {
@@ -111,32 +132,10 @@ int ifci_increments(ifci_handle_t h, const ifci_system_t *sys, int max_order, co
     }
     fixed += ws_round((size_t)h1_off[ns] * 8) + ws_round((size_t)eri_off[ns] * 8);
 
-    // Davidson batches under a vector-memory cap
-    std::vector<ProbSpec> all(ns);
-    for (int x = 0; x < ns; x++) all[x] = ProbSpec{P.nA[x], (int)P.subsets[x].size(), nullptr, nullptr, 0.0, nullptr};
+    // Davidson batches under a vector-memory cap (the solves take their memory
+    // from the handle's Davidson workspace)
     const size_t cap = (size_t)120 << 30;
-    std::vector<std::pair<int, int>> batches;
-    size_t dav_max = 0;
-    {
-        int first = 0;
-        size_t acc = 0;
-        for (int x = 0; x < ns; x++) {
-            long long nstr = binom(P.nA[x], (int)P.subsets[x].size());
-            size_t vb = (size_t)(2 * (o.max_space + 1) + 1) * nstr * nstr * 8;
-            if (acc + vb > cap && x > first) {
-                batches.push_back({first, x});
-                first = x;
-                acc = 0;
-            }
-            acc += vb;
-        }
-        batches.push_back({first, ns});
-        for (auto &bt : batches) {
-            std::vector<ProbSpec> sp(all.begin() + bt.first, all.begin() + bt.second);
-            dav_max = std::max(dav_max, dav_workspace_bytes(sp, o));
-        }
-    }
-    IFCI_TRY(ws_reserve(h, fixed + dav_max));
+    IFCI_TRY(ws_reserve(h, fixed));
 
     const double *dh = sys->h, *dV = sys->eri;
     if (sys->on_host) {
@@ -183,20 +182,80 @@ int ifci_increments(ifci_handle_t h, const ifci_system_t *sys, int max_order, co
     std::vector<double> ex(ns, 0.0);
     std::vector<int> st(ns, IFCI_OK), its(ns, 0);
     int ret = IFCI_OK;
-    const size_t mark = h->ws_top;
-    for (auto &bt : batches) {
-        std::vector<ProbSpec> sp;
-        for (int x = bt.first; x < bt.second; x++)
-            sp.push_back(ProbSpec{P.nA[x], (int)P.subsets[x].size(), d_h1 + h1_off[x], d_eri + eri_off[x], ecore[x],
-                                  keep ? h->kept.vec + vec_off[x] : nullptr});
-        h->ws_top = mark;
-        int r = dav_solve_sectors(h, sp, o, ex.data() + bt.first, its.data() + bt.first, st.data() + bt.first, s);
-        if (r != IFCI_OK && r != IFCI_ERR_NOT_CONVERGED) return r;
-        if (r != IFCI_OK) ret = r;
+    // solves the listed sets, in batches under the vector-memory cap
+    auto solve_sets = [&](const std::vector<int> &xs) -> int {
+        size_t first = 0, acc = 0;
+        for (size_t j = 0; j <= xs.size(); j++) {
+            size_t vb = 0;
+            if (j < xs.size()) {
+                const long long nstr = binom(P.nA[xs[j]], (int)P.subsets[xs[j]].size());
+                vb = (size_t)(2 * (o.max_space + 1) + 1) * nstr * nstr * 8;
+            }
+            if (j == xs.size() || (acc + vb > cap && j > first)) {
+                std::vector<ProbSpec> sp;
+                for (size_t t = first; t < j; t++) {
+                    const int x = xs[t];
+                    sp.push_back(ProbSpec{P.nA[x], (int)P.subsets[x].size(), d_h1 + h1_off[x], d_eri + eri_off[x],
+                                          ecore[x], keep ? h->kept.vec + vec_off[x] : nullptr});
+                }
+                std::vector<double> e(sp.size());
+                std::vector<int> it(sp.size()), stt(sp.size());
+                const int r = dav_solve_sectors(h, sp, o, e.data(), it.data(), stt.data(), s);
+                if (r != IFCI_OK && r != IFCI_ERR_NOT_CONVERGED) return r;
+                if (r != IFCI_OK) ret = r;
+                for (size_t t = first; t < j; t++) {
+                    ex[xs[t]] = e[t - first];
+                    its[xs[t]] = it[t - first];
+                    st[xs[t]] = stt[t - first];
+                }
+                first = j;
+                acc = 0;
+            }
+            acc += vb;
+        }
+        return IFCI_OK;
+    };
+    const bool screen = o.cnb_threshold > 0 && max_order >= 3;
+    std::vector<char> included(ns, 1);
+    if (!screen) {
+        std::vector<int> all_x(ns);
+        for (int x = 0; x < ns; x++) all_x[x] = x;
+        IFCI_TRY(solve_sets(all_x));
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_ex, ex.data(), ns * 8, cudaMemcpyHostToDevice, s));
+        increments_kernel<<<(ns + 127) / 128, 128, 0, s>>>(ns, d_soff, d_sidx, d_ssgn, d_ex, d_e0, d_eps);
+        IFCI_LAUNCH_CHECK(h);
+    } else {
+        // connected n-body screening: sets of 1 and 2 bodies are all solved; the
+        // sets of each larger size after the increments of the smaller ones
+        char *d_incl = ws_take<char>(h, ns);
+        if (!d_incl) return set_error(h, IFCI_ERR_OOM, "increments: workspace (screening)");
+        std::vector<int> size_off(max_order + 2, 0);
+        for (int x = 0; x < ns; x++) size_off[P.subsets[x].size() + 1] = x + 1;
+        std::vector<double> eps_h(ns, 0.0);
+        for (int k = 1; k <= max_order; k++) {
+            const int x0 = size_off[k], x1 = size_off[k + 1];
+            std::vector<int> xs;
+            for (int x = x0; x < x1; x++) {
+                if (k >= 3) included[x] = cnb_connected(P.subsets[x], sys->nbody, eps_h, o.cnb_threshold) ? 1 : 0;
+                if (included[x]) xs.push_back(x);
+                else st[x] = IFCI_SCREENED;
+            }
+            IFCI_TRY(solve_sets(xs));
+            IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_ex + x0, ex.data() + x0, (size_t)(x1 - x0) * 8, cudaMemcpyHostToDevice, s));
+            IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_incl + x0, included.data() + x0, (size_t)(x1 - x0),
+                                             cudaMemcpyHostToDevice, s));
+            increments_rec_kernel<<<(x1 - x0 + 127) / 128, 128, 0, s>>>(x0, x1, d_soff, d_sidx, d_incl, d_ex, d_e0,
+                                                                         d_eps);
+            IFCI_LAUNCH_CHECK(h);
+            if (k + 1 <= max_order) {
+                IFCI_CUDA_TRY(h, cudaMemcpyAsync(eps_h.data() + x0, d_eps + x0, (size_t)(x1 - x0) * 8,
+                                                 cudaMemcpyDeviceToHost, s));
+                IFCI_CUDA_TRY(h, cudaStreamSynchronize(s));
+            }
+        }
+        for (int x = 0; x < ns; x++)
+            if (!included[x]) ex[x] = std::nan("");
     }
-    IFCI_CUDA_TRY(h, cudaMemcpyAsync(d_ex, ex.data(), ns * 8, cudaMemcpyHostToDevice, s));
-    increments_kernel<<<(ns + 127) / 128, 128, 0, s>>>(ns, d_soff, d_sidx, d_ssgn, d_ex, d_e0, d_eps);
-    IFCI_LAUNCH_CHECK(h);
     total_kernel<<<1, 32, 0, s>>>(ns, d_eps, d_e0, d_tot);
     IFCI_LAUNCH_CHECK(h);
     IFCI_CUDA_TRY(h, cudaMemcpyAsync(eps, d_eps, ns * 8, cudaMemcpyDeviceToHost, s));
@@ -207,6 +266,8 @@ int ifci_increments(ifci_handle_t h, const ifci_system_t *sys, int max_order, co
     if (status) std::copy(st.begin(), st.end(), status);
     if (iters) std::copy(its.begin(), its.end(), iters);
     if (keep) {
+        h->kept.screened = screen;
+        h->kept.included = included;
         h->kept.valid = true;
         h->kept.nbody = sys->nbody;
         h->kept.max_order = max_order;
@@ -214,6 +275,8 @@ int ifci_increments(ifci_handle_t h, const ifci_system_t *sys, int max_order, co
         h->kept.body_offset.assign(sys->body_offset, sys->body_offset + sys->nbody + 1);
         h->kept.vec_off = vec_off;
     }
+    for (int x = 0; x < ns; x++)
+        if (st[x] != IFCI_OK && st[x] != IFCI_SCREENED) ret = IFCI_ERR_NOT_CONVERGED;
     if (ret != IFCI_OK) set_error(h, ret, "increments: some body sets did not converge");
     return ret;
 }

@@ -122,10 +122,10 @@ psp_select_kernel(const DavProb *__restrict__ probs, long long *__restrict__ pid
         bv[u] = 1e300;
         bi[u] = 0x7fffffffffffffffll;
     }
-    const int n = p.nstr;
+    const int n = p.nb;
     for (long long I = threadIdx.x; I < p.ndet; I += kSelThreads) {
         const int a = (int)(I / n), b = (int)(I % n);
-        if (a > b) continue;
+        if (p.sym && a > b) continue;
         double v = p.hd[I];
         long long i = I;
         if (v < bv[kSelPer - 1] || (v == bv[kSelPer - 1] && i < bi[kSelPer - 1])) {
@@ -168,7 +168,7 @@ psp_select_kernel(const DavProb *__restrict__ probs, long long *__restrict__ pid
             __syncthreads();
         }
     }
-    const long long nsym = (long long)n * (n + 1) / 2;
+    const long long nsym = p.ndim;
     const int P = nsym < kPsp ? (int)nsym : kPsp;
     if (threadIdx.x < kPsp) pidx[blockIdx.x * kPsp + threadIdx.x] = threadIdx.x < P ? si[threadIdx.x] : -1;
     if (threadIdx.x == 0) pcount[blockIdx.x] = P;
@@ -189,23 +189,26 @@ psp_solve_kernel(const DavProb *__restrict__ probs, const HdiagDesc *__restrict_
     const HdiagDesc d = hdd[blockIdx.x];
     const int P = pcount[blockIdx.x];
     const int t = threadIdx.x;
-    const int n = p.nstr;
+    const int n = p.nb;
     const double rs2 = 0.7071067811865476;
-    // row t of A: <u_t|H|u_c>, every term of the pair functions written out
+    // row t of A: <u_t|H|u_c>, every term of the pair functions written out (in
+    // an off-diagonal block, whose spin-flip image is not iterated, u_K = |K>)
     if (t < P) {
         const long long K = pidx[blockIdx.x * kPsp + t];
         const int ka = (int)(K / n), kb = (int)(K % n);
         for (int c = 0; c < P; c++) {
             const long long L = pidx[blockIdx.x * kPsp + c];
             const int la = (int)(L / n), lb = (int)(L % n);
-            const int nbra = ka == kb ? 1 : 2, nket = la == lb ? 1 : 2;
+            const int nbra = (ka == kb || !p.sym) ? 1 : 2, nket = (la == lb || !p.sym) ? 1 : 2;
             const double f = (nbra == 2 ? rs2 : 1.0) * (nket == 2 ? rs2 : 1.0);
             double v = 0.0;
             for (int x = 0; x < nbra; x++)
                 for (int y = 0; y < nket; y++) {
+                    // (row, column) local indices of the bra and ket determinants
                     const int ba = x ? kb : ka, bb = x ? ka : kb, ca = y ? lb : la, cb = y ? la : lb;
-                    v += h_element(d.n, d.h1, d.eri, (uint32_t)d.strings[ba], (uint32_t)d.strings[bb],
-                                   (uint32_t)d.strings[ca], (uint32_t)d.strings[cb]);
+                    v += h_element(d.n, d.h1, d.eri, (uint32_t)d.strings[blk_row(p, ba)],
+                                   (uint32_t)d.strings[blk_col(p, bb)], (uint32_t)d.strings[blk_row(p, ca)],
+                                   (uint32_t)d.strings[blk_col(p, cb)]);
                 }
             A[t * kPsp + c] = f * v;
             V[t * kPsp + c] = t == c ? 1.0 : 0.0;
@@ -282,7 +285,8 @@ psp_solve_kernel(const DavProb *__restrict__ probs, const HdiagDesc *__restrict_
     }
     // the nv lowest eigenvalues' columns, each sign fixed by its largest component
     int nv, ns;
-    start_block(n, max_space, &nv, &ns);
+    start_block(p.ndim, max_space, p.seed != nullptr, &nv, &ns);
+    if (p.seed) return;   // started from its own vector: no P-space guess
     __shared__ int cols[kStartP];
     if (t == 0) {
         // eigenvalues in ascending order; each eigenvector's block is the block
@@ -358,7 +362,7 @@ psp_solve_kernel(const DavProb *__restrict__ probs, const HdiagDesc *__restrict_
                 if (fabs(V[i * kPsp + col]) > fabs(V[g * kPsp + col])) g = i;
             const double y = (V[g * kPsp + col] < 0 ? -1.0 : 1.0) * V[t * kPsp + col];
             double *Br = p.B + (long long)r * p.ndet;
-            if (ka == kb) {
+            if (ka == kb || !p.sym) {
                 Br[K] = y;
             } else {
                 Br[K] = y * rs2;
@@ -368,7 +372,7 @@ psp_solve_kernel(const DavProb *__restrict__ probs, const HdiagDesc *__restrict_
         if (ns >= 0) {   // the random vector becomes exactly orthogonal to the block
             double *Bn = p.B + (long long)ns * p.ndet;
             Bn[K] = 0.0;
-            Bn[KT] = 0.0;
+            if (p.sym) Bn[KT] = 0.0;
         }
     }
 }
@@ -419,8 +423,8 @@ size_t psp_workspace_bytes(int nprob) {
 // start vector on the P-space determinants and stores its |.|^2 per item in
 // part (the caller normalises it).
 int launch_pspace_start(ifci_handle_t h, const DavBatch &b, const HdiagDesc *d_hd, cudaStream_t s) {
-    long long *pidx = ws_take<long long>(h, (size_t)b.nprob * kPsp);
-    int *pcount = ws_take<int>(h, (size_t)b.nprob);
+    long long *pidx = b.d_pidx;
+    int *pcount = b.d_pcount;
     if (!pidx || !pcount) return set_error(h, IFCI_ERR_OOM, "davidson: workspace (P-space)");
     psp_select_kernel<<<b.nprob, kSelThreads, 0, s>>>(b.d_probs, pidx, pcount);
     IFCI_LAUNCH_CHECK(h);

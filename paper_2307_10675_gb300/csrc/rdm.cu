@@ -277,6 +277,32 @@ extern "C" int ifci_rdm_backward(ifci_handle_t h, const ifci_system_t *sys, int 
     }
     SubsetPlan P;
     plan_subsets(sys, max_order, P);
+    // expansion weights: closed form, or (screened expansion) the derivative of
+    // the recursion of Eqs. 2-5 at the forward call's inclusion pattern; the
+    // screened sets (no vector, weight 0) leave the plan
+    std::vector<double> wts(P.subsets.size());
+    std::vector<long long> kvec_off;
+    {
+        const bool scr = h->kept.screened && h->kept.included.size() == P.subsets.size();
+        if (scr) wts = screened_weights(P, h->kept.included);
+        else
+            for (size_t x = 0; x < P.subsets.size(); x++)
+                wts[x] = (double)expansion_weight(sys->nbody, (int)P.subsets[x].size(), max_order);
+        SubsetPlan Q;
+        Q.orbs = P.orbs;
+        std::vector<double> w2;
+        for (size_t x = 0; x < P.subsets.size(); x++) {
+            if (scr && !h->kept.included[x]) continue;
+            Q.subsets.push_back(P.subsets[x]);
+            Q.nA.push_back(P.nA[x]);
+            Q.nC.push_back(P.nC[x]);
+            Q.orb_off.push_back(P.orb_off[x]);
+            kvec_off.push_back(h->kept.vec_off[x]);
+            w2.push_back(wts[x]);
+        }
+        P = std::move(Q);
+        wts = std::move(w2);
+    }
     const int ns = (int)P.subsets.size();
 
     // problems, D+ waves and split-K jobs
@@ -293,10 +319,10 @@ extern "C" int ifci_rdm_backward(ifci_handle_t h, const ifci_system_t *sys, int 
         r.nstr = (int)binom(r.n, m);
         r.nexc = m * (r.n - m + 1);
         r.ndet = (long long)r.nstr * r.nstr;
-        r.c = h->kept.vec + h->kept.vec_off[x];
-        const long long wy = expansion_weight(sys->nbody, m, max_order);
-        r.w = (double)wy * grad_out;
-        wsum += (double)wy;
+        r.c = h->kept.vec + kvec_off[x];
+        const double wy = wts[x];
+        r.w = wy * grad_out;
+        wsum += wy;
         const long long need = (long long)(r.np + 1) * r.ndet;
         maxd = std::max(maxd, need);
         dtotal += need;

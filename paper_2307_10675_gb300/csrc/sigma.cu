@@ -154,8 +154,8 @@ scatter_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__
 
 // Quantised copy of c for the tensor-core gathers, written into the D buffer
 // (which those paths do not need): FP32 for BF16, and for FP64E the fixed
-// point integer round(c * 2^38 / dscale), so that their gathers run in FP32 or
-// integer arithmetic (GB300 issues FP64 at a small fraction of FP32).
+// point integer X = round(c * 2^38 / dscale), so that their gathers run in FP32
+// or integer arithmetic (GB300 issues FP64 at a small fraction of FP32).
 template <int KIND>
 __global__ void __launch_bounds__(kGatherChunk)
 quantise_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__ items, char *__restrict__ qbuf) {
@@ -313,6 +313,28 @@ int upload_plan(ifci_handle_t h, SigmaPlan &plan, cudaStream_t s) {
         return set_error(h, IFCI_ERR_OOM, "sigma plan: workspace too small");
     IFCI_CUDA_TRY(h, cudaMemcpyAsync(plan.d_probs, plan.probs.data(), plan.probs.size() * sizeof(SigmaProb),
                                      cudaMemcpyHostToDevice, s));
+    if (!plan.items.empty())
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(plan.d_items, plan.items.data(), plan.items.size() * sizeof(WorkItem),
+                                         cudaMemcpyHostToDevice, s));
+    if (!plan.tiles.empty())
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(plan.d_tiles, plan.tiles.data(), plan.tiles.size() * sizeof(WorkItem),
+                                         cudaMemcpyHostToDevice, s));
+    if (!plan.tctiles.empty())
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(plan.d_tctiles, plan.tctiles.data(),
+                                         plan.tctiles.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+    return IFCI_OK;
+}
+
+// Copies the plan's descriptor arrays to the device arrays the caller set in
+// plan.d_probs, d_items, d_tiles, d_tctiles (each holding at least one entry).
+int upload_plan_to(ifci_handle_t h, SigmaPlan &plan, cudaStream_t s) {
+    for (const SigmaProb &p : plan.probs)
+        if (p.sym && !p.pmap) return set_error(h, IFCI_ERR_INVALID_ARG, "sigma plan: symmetric problem without pair map");
+    if (!plan.d_probs || !plan.d_items || !plan.d_tiles || !plan.d_tctiles)
+        return set_error(h, IFCI_ERR_INVALID_ARG, "sigma plan: device arrays not set");
+    if (!plan.probs.empty())
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(plan.d_probs, plan.probs.data(), plan.probs.size() * sizeof(SigmaProb),
+                                         cudaMemcpyHostToDevice, s));
     if (!plan.items.empty())
         IFCI_CUDA_TRY(h, cudaMemcpyAsync(plan.d_items, plan.items.data(), plan.items.size() * sizeof(WorkItem),
                                          cudaMemcpyHostToDevice, s));

@@ -70,6 +70,8 @@ int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision
 size_t plan_device_bytes(const SigmaPlan &plan);
 // Copies the plan's descriptor arrays to device memory taken from the workspace.
 int upload_plan(ifci_handle_t h, SigmaPlan &plan, cudaStream_t s);
+// The same into device arrays the caller has already set in the plan.
+int upload_plan_to(ifci_handle_t h, SigmaPlan &plan, cudaStream_t s);
 // Launches every wave: D, G are device buffers of at least max_delems
 // elements of the precision's storage type (8 B for FP64, 4 B otherwise).
 int run_sigma(ifci_handle_t h, const SigmaPlan &plan, int precision, void *D, void *G, cudaStream_t s);

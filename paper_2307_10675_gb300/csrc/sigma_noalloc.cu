@@ -1,6 +1,8 @@
 // ifci_sigma_noalloc: the FP64 sigma build of ifci_sigma with all of its
 // scratch memory in one fixed, file-scope device array, for callers that may
 // not allocate device memory themselves (see include/ifci.h).
+#include <atomic>
+
 #include "hamiltonian.cuh"
 #include "sigma.cuh"
 
@@ -14,7 +16,16 @@ namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB on every device that loads the library
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
-void *g_scratch_addr[kMaxDevices];  // device address of g_static_scratch, per device
+// device address of g_static_scratch, per device (written once per device;
+// host threads may race on the first call, and each stores the same address)
+std::atomic<void *> g_scratch_addr[kMaxDevices];
+
+// the two descriptors of the call, passed by value so that no host buffer
+// outlives the call
+__global__ void write_desc_kernel(FoldDesc *fd, FoldDesc f, SigmaProb *pd, SigmaProb p) {
+    *fd = f;
+    *pd = p;
+}
 
 // Work lists of the single problem: gather/scatter items and 64 x 64 contraction tiles.
 __global__ void fill_work_kernel(WorkItem *items, int nitem, WorkItem *tiles, int ntile, int np, long long ndet) {
@@ -52,17 +63,17 @@ extern "C" int ifci_sigma_noalloc(const ifci_strings_t *str, const double *h1, c
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return IFCI_ERR_CUDA;
-    if (!g_scratch_addr[dev]) {
+    void *addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!addr) {
         // once per device, with that device current: the host-side symbol is
         // only a stand-in, the kernels need the device address
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+        if (cudaGetSymbolAddress(&addr, g_static_scratch) != cudaSuccess || !addr) {
             cudaGetLastError();
             return IFCI_ERR_CUDA;
         }
-        g_scratch_addr[dev] = p;
+        g_scratch_addr[dev].store(addr, std::memory_order_release);
     }
-    char *base = static_cast<char *>(g_scratch_addr[dev]);
+    char *base = static_cast<char *>(addr);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         char *p = base + off;
@@ -84,11 +95,8 @@ extern "C" int ifci_sigma_noalloc(const ifci_strings_t *str, const double *h1, c
     p.ndet = ndet; p.stride = ndet; p.exc = str->exc; p.W = W;
     p.cbase = c; p.sbase = sigma; p.doff = 0;
     // every scratch byte used below is written before it is read: nothing needs clearing
-    if (cudaMemcpyAsync(fd, &f, sizeof(f), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(pd, &p, sizeof(p), cudaMemcpyHostToDevice, s) != cudaSuccess) {
-        cudaGetLastError();
-        return IFCI_ERR_CUDA;
-    }
+    write_desc_kernel<<<1, 1, 0, s>>>(fd, f, pd, p);
+    if (cudaGetLastError() != cudaSuccess) return IFCI_ERR_CUDA;
     if (launch_fold_raw(fd, np, s) != cudaSuccess) return IFCI_ERR_CUDA;
     int nfill = nitem > ntile ? nitem : ntile;
     fill_work_kernel<<<(nfill + 255) / 256, 256, 0, s>>>(items, nitem, tiles, ntile, np, ndet);

@@ -1,6 +1,10 @@
 // Body sets of an iFCI system and their frozen-body orbital lists (host side),
 // shared by ifci_increments and ifci_rdm_backward.
 #pragma once
+#include <algorithm>
+#include <cmath>
+#include <map>
+
 #include "common.cuh"
 
 namespace ifci {
@@ -93,5 +97,57 @@ inline void plan_subsets(const ifci_system_t *sys, int max_order, SubsetPlan &P)
     }
 }
 
+
+// Position of the pair {a, b} (a < b) in the subset order (all single bodies first).
+inline long long pair_position(int nbody, int a, int b) {
+    return nbody + (long long)a * nbody - (long long)a * (a + 1) / 2 + (b - a - 1);
+}
+
+// Connected n-body screening: the bodies of X, joined by the pairs of X with
+// |eps_pair| >= C, form one connected graph.
+inline bool cnb_connected(const std::vector<int> &X, int nbody, const std::vector<double> &eps, double C) {
+    const int k = (int)X.size();
+    std::vector<char> seen(k, 0);
+    std::vector<int> stack{0};
+    seen[0] = 1;
+    int nseen = 1;
+    while (!stack.empty()) {
+        const int i = stack.back();
+        stack.pop_back();
+        for (int j = 0; j < k; j++) {
+            if (seen[j]) continue;
+            const int a = std::min(X[i], X[j]), b = std::max(X[i], X[j]);
+            if (std::fabs(eps[pair_position(nbody, a, b)]) >= C) {
+                seen[j] = 1;
+                nseen++;
+                stack.push_back(j);
+            }
+        }
+    }
+    return nseen == k;
+}
+
+// d(sum_X eps_X) / d E_c(Y) for the recursion of Eqs. 2-5 with screened sets
+// (included[x] = 0) counting as zero: eps_X = E_c(X) - sum_{Y proper subset} eps_Y.
+// The coefficients of eps_X over the E_c of its subsets follow the same
+// recursion; the weights are their sums over the included sets.
+inline std::vector<double> screened_weights(const SubsetPlan &P, const std::vector<char> &included) {
+    const int ns = (int)P.subsets.size();
+    std::vector<std::vector<std::pair<int, double>>> coef(ns);
+    std::vector<double> w(ns, 0.0);
+    for (int x = 0; x < ns; x++) {
+        if (!included[x]) continue;
+        std::map<int, double> cx;
+        cx[x] += 1.0;
+        for (long long t = P.sub_off[x]; t < P.sub_off[x + 1]; t++) {
+            const int y = P.sub_idx[t];
+            if (y == x || !included[y]) continue;
+            for (const auto &e : coef[y]) cx[e.first] -= e.second;
+        }
+        coef[x].assign(cx.begin(), cx.end());
+        for (const auto &e : coef[x]) w[e.first] += e.second;
+    }
+    return w;
+}
 
 }  // namespace ifci

@@ -97,6 +97,7 @@ def test_davidson_default_opts_from_the_library():
     assert (o.e_tol, o.r_tol) == (1e-10, 1e-6)
     assert o.hi_precision == _capi.IFCI_FP64E
     assert o.det_budget == 0 and o.graph_iters == 0
+    assert o.sector_passes == 0 and o.decouple_tol == 1e-5
 
 
 def test_sigma_flag_matches_the_header():

@@ -538,3 +538,57 @@ def test_oracle_gradient_obeys_euler_identity(order):
     e, dh, dV = fci.ifci_gradient(s, order, method="dense")
     euler = float(np.sum(s.h * dh) + np.sum(s.eri_packed() * dV))
     assert euler == pytest.approx(e, abs=1e-10)
+
+
+# ---------------------------------------------------------------- connected n-body screening
+
+@pytest.fixture(scope="module")
+def chain4x2_order4():
+    s = chain_4x2()
+    return s, fci.ifci_energies(s, 4)
+
+
+def test_cnb_screening_off_equals_the_full_expansion(chain4x2_order4):
+    s, full = chain4x2_order4
+    pair_min = min(abs(v) for X, v in full[2].items() if len(X) == 2)
+    b = fci.ifci_energies(s, 4, cnb=0.5 * pair_min)       # every pair is an edge: nothing screened
+    assert b[3] == pytest.approx(full[3], abs=1e-10)
+    assert set(b[1]) == set(full[1])
+
+
+def test_cnb_screening_keeps_exactly_the_connected_sets(chain4x2_order4):
+    """The kept 3- and 4-body sets are the sets whose graph of pair increments
+    at or above C is connected, checked with networkx on the pair table;
+    screened increments are zero and the others follow Eqs. 2-5 with them."""
+    nx = pytest.importorskip("networkx")
+    s, full = chain4x2_order4
+    eps_full = full[2]
+    pair_mags = sorted(abs(v) for X, v in eps_full.items() if len(X) == 2)
+    C = 0.5 * (pair_mags[2] + pair_mags[3])          # keeps the three largest pairs
+    e0, ex, eps, total = fci.ifci_energies(s, 4, cnb=C)
+    kept = 0
+    for X in fci.body_subsets(4, 4):
+        if len(X) < 3:
+            assert X in ex
+            continue
+        g = nx.Graph()
+        g.add_nodes_from(X)
+        g.add_edges_from(p for p in itertools.combinations(X, 2) if abs(eps_full[p]) >= C)
+        assert (X in ex) == nx.is_connected(g), X
+        if X in ex:
+            kept += 1
+            rec = ex[X] - e0 - sum(eps[Y] for j in range(1, len(X)) for Y in itertools.combinations(X, j))
+            assert eps[X] == pytest.approx(rec, abs=1e-13)
+            assert ex[X] == pytest.approx(full[1][X], abs=1e-9)   # a kept set is solved as before
+        else:
+            assert eps[X] == 0.0
+    assert 0 < kept < 5
+    assert total == pytest.approx(e0 + sum(eps.values()), abs=1e-13)
+
+
+def test_cnb_screening_everything_above_two_bodies_gives_the_order_2_total(chain4x2_order4):
+    s, _ = chain4x2_order4
+    two = fci.ifci_energies(s, 2)[3]
+    scr = fci.ifci_energies(s, 4, cnb=1e3)
+    assert scr[3] == pytest.approx(two, abs=1e-13)
+    assert all(len(X) <= 2 for X in scr[1])

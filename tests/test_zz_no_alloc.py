@@ -68,3 +68,31 @@ def test_noalloc_sigma_rejects_problems_beyond_the_array():
         c = torch.zeros(t.nstr * t.nstr, dtype=torch.float64, device=DEV)
         out = torch.zeros_like(c)
         assert ifci.ifci_sigma_noalloc(t, h1, eri, c, out) == 1      # IFCI_ERR_INVALID_ARG
+
+
+def test_noalloc_sigma_allocates_nothing_once_set_up():
+    """After one call on the device (which loads the library's device code and
+    the fixed array), later calls succeed while the caller's allocator holds
+    nearly all free device memory, and leave the free memory unchanged."""
+    torch.cuda.set_device(DEV)
+    with ifci.Handle(0, 0) as h:
+        t, h1, eri = _problem(h, chain_4x2(), (0, 1, 2))
+        c = torch.tensor(random_ci_vector(t.nstr, t.nstr, seed=3), device=DEV)
+        ref = ifci.ifci_sigma(h, t, h1, eri, c)
+        out = torch.empty_like(c)
+        assert ifci.ifci_sigma_noalloc(t, h1, eri, c, out) == 0      # set-up call
+        torch.cuda.synchronize()
+        free, _ = torch.cuda.mem_get_info()
+        got = torch.full_like(c, float("nan"))
+        hold = torch.empty(max(0, free - (512 << 20)), dtype=torch.uint8, device=DEV)   # leave 512 MiB
+        try:
+            torch.cuda.synchronize()
+            before, _ = torch.cuda.mem_get_info()
+            assert ifci.ifci_sigma_noalloc(t, h1, eri, c, got) == 0
+            torch.cuda.synchronize()
+            after, _ = torch.cuda.mem_get_info()
+            assert after == before
+            np.testing.assert_allclose(got.cpu().numpy(), ref.cpu().numpy(), rtol=0, atol=1e-10)
+        finally:
+            del hold
+            torch.cuda.empty_cache()
