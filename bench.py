@@ -1,15 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the iFCI increment CI solve on one GB300 (or N, one rank each).
 
-One step = the whole hot path over one synthetic workload: every body set of
-the 24-body uneven chain up to 3 bodies (24 + 276 + 2024 = 2324 CI problems,
-largest CAS(6e,18o) with 665,856 determinants), frozen-body Hamiltonians,
-batched Davidson to convergence, and the FP64 increments with their sum,
-all through ``ifci_increments`` with device-resident integrals.
+One step = the whole hot path over one synthetic workload, through
+``ifci_increments`` with device-resident integrals: every body set of the
+40-body uneven chain (seed 2310; eight bodies each of 2-6 orbitals, 160
+orbitals) up to 3 bodies (40 + 780 + 9880 = 10,700 CI problems, largest
+CAS(6e,18o) with 665,856 determinants), frozen-body Hamiltonians, the exact
+blocks of decoupled bodies, batched Davidson to convergence, and the FP64
+increments with their sum.  ``--workload c1`` takes the 24-body chain (2324
+problems) instead.
 
-Default path ("fp64e"): every sigma contraction FP64-accurate on BF16 tensor
-cores, all Davidson arithmetic FP64.  The same run also times the plain FP64
-path and the mixed BF16 path once each (``other_paths``) on the same GPU.
+Default path ("fp64e"): every sigma contraction FP64-accurate on the FP16
+tensor cores (digit slices, exact level sums), all Davidson arithmetic FP64.
+The timed steps run without per-kernel profiling; one more step with the
+library's per-kernel CUDA-event profiling gives the kernel-class times and
+the roofline.  The plain FP64 path and the mixed BF16 path are timed against
+FP64E on a seeded sample of the same body sets (``paths_sample``).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 a bounded sample of the same workload instead.
@@ -44,22 +50,39 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c4", choices=["c4", "c1"],
+                    help="c4: 40-body chain (10,700 CI problems); c1: 24-body chain (2324)")
     ap.add_argument("--precision", default="fp64e", choices=["fp64", "fp32", "bf16", "fp64e"])
-    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 and mixed comparison runs")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 and mixed comparison on the sample")
+    ap.add_argument("--compare-fraction", type=float, default=0.05,
+                    help="seeded fraction of the 3-body sets in the path comparison (all 1- and 2-body sets)")
     ap.add_argument("--max-order", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sample-seconds", type=float, default=20.0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the autotuner (max_space, det_budget, graph_iters) and use the library defaults")
+    ap.add_argument("--autotune-fraction", type=float, default=0.05,
+                    help="seeded fraction of the largest body sets in the autotuner's sample")
+    ap.add_argument("--dump", default="", help="--case c4: directory for per-set energies")
     ap.add_argument("--det-budget", type=int, default=0,
                     help="determinants per sigma wave (0: library default)")
     ap.add_argument("--case", default="increments", choices=["increments", "sigma", "c2", "c4"],
                     help="sigma: time ifci_sigma alone on the workload's largest problem, CAS(6e,18o) "
                          "(the small case for kernel profiles); c2: one CAS(14e,14o) CI per precision; "
-                         "c4: 3-body iFCI of the 40-body chain per precision, plus the RDM backward")
+                         "c4: 3-body iFCI of the 40-body chain in every precision on all 10,700 sets "
+                         "(totals and per-set differences), plus the RDM backward")
     return ap.parse_args()
 
 
 # ---------------------------------------------------------------- workload
+
+R_TOL, E_TOL = 1e-6, 1e-10
+WORKLOAD_NAMES = {
+    "c4": "chain-40-uneven, iFCI to 3 bodies, 10,700 CI problems, max CAS(6e,18o)",
+    "c1": "chain-24-uneven, iFCI to 3 bodies, 2324 CI problems, max CAS(6e,18o)",
+}
+
 
 def max_over_ranks(value: float, dist, device) -> float:
     """The slowest rank's time (every rank returns it); ``dist`` None = one rank."""
@@ -71,10 +94,12 @@ def max_over_ranks(value: float, dist, device) -> float:
     return float(t.item())
 
 
-def workload(rank: int = 0):
-    from synth import chain_24_uneven
-    # weak scaling: rank r solves its own chain (seed 2308 + r) of the same shape
-    return chain_24_uneven(seed=2308 + rank)
+def workload(rank: int = 0, name: str = "c4"):
+    """Weak scaling: rank r solves its own chain (base seed + r) of the same shape."""
+    from synth import chain_24_uneven, chain_40_uneven
+    if name == "c1":
+        return chain_24_uneven(seed=2308 + rank)
+    return chain_40_uneven(seed=2310 + rank)
 
 
 def cost_of(n: int, m: int):
@@ -91,6 +116,16 @@ def subset_sizes(chain, max_order):
         for X in itertools.combinations(range(chain.nbody), k):
             out.append((X, sum(chain.body_sizes[b] for b in X), k))
     return out
+
+
+def compare_sample(chain, max_order, fraction, seed=7):
+    """Seeded sample of the workload's body sets for the path comparison:
+    every set of size < max_order and a fraction of the largest ones."""
+    subs = subset_sizes(chain, max_order)
+    top = [i for i, (_, _, k) in enumerate(subs) if k == max_order]
+    rng = np.random.default_rng(seed)
+    pick = {top[j] for j in rng.choice(len(top), max(1, int(round(fraction * len(top)))), replace=False)}
+    return [s for i, s in enumerate(subs) if s[2] < max_order or i in pick]
 
 
 # ---------------------------------------------------------------- clocks
@@ -150,42 +185,54 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- CPU oracle baseline
 
+def oracle_conn(n, m):
+    """Determinants connected to one determinant (itself included) by H."""
+    s1 = m * (n - m)
+    s2 = math.comb(m, 2) * math.comb(n - m, 2)
+    return 1 + 2 * (s1 + s2) + s1 * s1
+
+
 def oracle_baseline(chain, max_order, seconds, seed=11):
     """Times the oracle on a seeded sample of the workload's body sets for about
-    ``seconds`` and extrapolates the whole workload's time with the cost model
-    t(X) ~ ndet(X) * connected determinants per row(X)."""
+    ``seconds`` and extrapolates the whole workload's time.  Two regimes, as
+    the oracle solves them: dense eigh (ndet <= oracle DENSE_MAX), every such
+    set timed or its mean taken; Lanczos (matrix-free Slater–Condon matvecs),
+    calibrated on the sampled sets up to 30,000 determinants with the model
+    t = a * ndet * (determinants connected per row)."""
     from oracle import fci
     subs = subset_sizes(chain, max_order)
-
-    def conn(n, m):
-        s1 = m * (n - m)
-        s2 = math.comb(m, 2) * math.comb(n - m, 2)
-        return 1 + 2 * (s1 + s2) + s1 * s1
-
-    def model(n, m):
-        return math.comb(n, m) ** 2 * conn(n, m)
-
     rng = np.random.default_rng(seed)
     order = rng.permutation(len(subs))
     fci.lib()                       # build/load before timing
-    done, t_used, m_used = 0, 0.0, 0.0
-    for idx in order:
-        X, n, k = subs[idx]
-        if math.comb(n, k) ** 2 > 30000:
-            continue
+    dense = [i for i in order if math.comb(subs[i][1], subs[i][2]) ** 2 <= fci.DENSE_MAX]
+    lanc = [i for i in order if fci.DENSE_MAX < math.comb(subs[i][1], subs[i][2]) ** 2 <= 30000]
+    t_dense, n_dense, t_lanc, m_lanc, n_lanc = 0.0, 0, 0.0, 0.0, 0
+    for i in dense:
+        X, n, k = subs[i]
         t0 = time.perf_counter()
         fci.solve_subsystem(chain, X)
-        t_used += time.perf_counter() - t0
-        m_used += model(n, k)
-        done += 1
-        if t_used > seconds:
+        t_dense += time.perf_counter() - t0
+        n_dense += 1
+        if t_dense > 0.25 * seconds:
             break
-    total_model = sum(model(n, k) for _, n, k in subs)
-    t_total = t_used / m_used * total_model
+    for i in lanc:
+        X, n, k = subs[i]
+        t0 = time.perf_counter()
+        fci.solve_subsystem(chain, X)
+        t_lanc += time.perf_counter() - t0
+        m_lanc += math.comb(n, k) ** 2 * oracle_conn(n, k)
+        n_lanc += 1
+        if t_lanc > 0.75 * seconds:
+            break
+    nd_dense = sum(1 for _, n, k in subs if math.comb(n, k) ** 2 <= fci.DENSE_MAX)
+    model_rest = sum(math.comb(n, k) ** 2 * oracle_conn(n, k) for _, n, k in subs
+                     if math.comb(n, k) ** 2 > fci.DENSE_MAX)
+    t_total = t_dense / max(n_dense, 1) * nd_dense + t_lanc / max(m_lanc, 1.0) * model_rest
     return {"value": len(subs) / t_total, "unit": UNIT, "cores": fci.num_threads(), "kind": "oracle",
-            "sample": (f"{done} seeded body sets with <= 30,000 determinants timed in {t_used:.1f} s; "
-                       f"whole-workload time extrapolated by ndet x connections per row "
-                       f"({t_total:.0f} s for {len(subs)} sets)")}
+            "sample": (f"{n_dense} dense and {n_lanc} Lanczos body sets (<= 30,000 determinants) of the workload, "
+                       f"seeded, timed in {t_dense + t_lanc:.1f} s; whole-workload time extrapolated per regime "
+                       f"(dense: mean per set; Lanczos: ndet x connected determinants per row), "
+                       f"{t_total:.0f} s for {len(subs)} sets")}
 
 
 # ---------------------------------------------------------------- main
@@ -200,7 +247,7 @@ def main():
         if rank != 0:
             return 0
         steps = args.steps if args.steps is not None else 1
-        chain = workload(0)
+        chain = workload(0, args.workload)
         per = max(3.0, args.sample_seconds / 2)
         for _ in range(args.warmup):
             oracle_baseline(chain, args.max_order, per)
@@ -214,8 +261,8 @@ def main():
         line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": steps, "warmup": args.warmup,
                 "ms_per_step": 1000 * el / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": {"workload": "chain-24-uneven, iFCI to 3 bodies, 2324 CI problems, max CAS(6e,18o)",
-                           "seed": chain.seed, "sample": "bounded oracle sample per step"},
+                "config": {"workload": WORKLOAD_NAMES[args.workload], "seed": chain.seed,
+                           "sample": "bounded oracle sample per step"},
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                                  "sample": r["sample"]},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -238,55 +285,66 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    steps = args.steps if args.steps is not None else (1 if args.precision == "fp64" else 3)
+    steps = args.steps if args.steps is not None else 3
     warmup = max(3, args.warmup)
 
-    chain = workload(rank)
+    chain = workload(rank, args.workload)
     sysd = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=dev),
                              torch.tensor(chain.eri_packed(), device=dev))
     subs = subset_sizes(chain, args.max_order)
     nsub = len(subs)
     handle = ifci.Handle(0, local)
 
+    tuned = {"max_space": 12, "det_budget": args.det_budget, "graph_iters": 0}
+    tune_info = None
+    if not args.no_autotune:
+        from paper_2307_10675_gb300 import autotune
+        # the largest body sets carry nearly all of the cost: the sample is a seeded fraction of them
+        sample = [X for X, _, k in compare_sample(chain, args.max_order, args.autotune_fraction, seed=5)
+                  if k == args.max_order]
+        t0 = time.perf_counter()
+        res = autotune.autotune(handle, sysd, sample, args.precision, r_tol=R_TOL, e_tol=E_TOL)
+        tuned = res["params"]
+        tune_info = {"params": tuned, "sample_sets": len(sample), "seconds": time.perf_counter() - t0,
+                     "table": [[c["params"], round(c["seconds"], 4), c["accepted"]] for c in res["table"]]}
+
     def opts_for(prec):
-        return ifci.davidson_opts(prec, r_tol=1e-6, e_tol=1e-10, max_iter=200, det_budget=args.det_budget)
+        return ifci.davidson_opts(prec, r_tol=R_TOL, e_tol=E_TOL, max_iter=300, **tuned)
 
-    def timed(prec, nsteps, nwarm, profile=False):
-        for _ in range(nwarm):
-            ifci.ifci_increments(handle, sysd, args.max_order, opts_for(prec))
-        torch.cuda.synchronize(dev)
-        if profile:
-            handle.profile_enable(True)
-        l0 = handle.launches()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        stream = torch.cuda.current_stream(dev)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for _ in range(nsteps):
-            out = ifci.ifci_increments(handle, sysd, args.max_order, opts_for(prec))
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
-        if dist:
-            dist.barrier()
-        ms = ev0.elapsed_time(ev1)
-        prof = handle.profile_read() if profile else None
-        if profile:
-            handle.profile_enable(False)
-        ms = max_over_ranks(ms, dist, dev)
-        return out, ms / nsteps, prof, handle.launches() - l0
-
-    clocks = ClockSampler(local)
+    stream = torch.cuda.current_stream(dev)
     for _ in range(warmup):
         ifci.ifci_increments(handle, sysd, args.max_order, opts_for(args.precision))
+    torch.cuda.synchronize(dev)
+
+    # ---- timed steps: no per-kernel profiling
+    clocks = ClockSampler(local)
     clocks.start()
-    out, ms_step, prof, launches = timed(args.precision, steps, 0, profile=True)
+    l0 = handle.launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        out = ifci.ifci_increments(handle, sysd, args.max_order, opts_for(args.precision))
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    launches = handle.launches() - l0
     clk = clocks.stop()
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1), dist, dev) / steps
     value = world * nsub / (ms_step / 1000.0)
 
+    # ---- one profiled step: kernel-class times (CUDA events around every launch)
+    handle.profile_enable(True)
+    outp = ifci.ifci_increments(handle, sysd, args.max_order, opts_for(args.precision))
+    torch.cuda.synchronize(dev)
+    prof = handle.profile_read()
+    handle.profile_enable(False)
+
     # algorithmic sigma FLOPs of a step: sigma builds per problem x 2 ndet npair^2
-    its = out["iters"]
+    its = outp["iters"]
     flops_step = 0.0
     exec_step = 0.0
     gelems_step = 0.0
@@ -296,41 +354,42 @@ def main():
         flops_step += it * fl
         exec_step += it * executed_oz_flops(n, k)
         gelems_step += it * nd * (n * (n + 1) // 2)
-    sig_ms = sum(prof[k][0] for k in ("gather", "contract", "contract_hi", "scatter")) / steps
+    sig_ms = sum(prof[k][0] for k in ("gather", "contract", "contract_hi", "scatter"))
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     bf = peaks.get("bf16_tflops_sustained")
-    bf_src = "MEASURED_PEAKS.json bf16_tflops_sustained" if bf else "fallback 1700 TFLOP/s (sustained)"
+    bf_src = "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" if bf else \
+        "fallback 1700 TFLOP/s sustained (of fallback)"
     bf = bf or 1700.0
     fp64_peak_tf, fp64_how = _dgemm_peak(dev)
     if args.precision == "fp64":
-        c_ms = prof["contract"][0] / steps
-        fp64_peak = fp64_peak_tf
+        c_ms = prof["contract"][0]
         ach = flops_step / (c_ms / 1000.0) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                "traffic": None, "kernel": "contract_simt_kernel<double>", "peak_source": fp64_how}
+        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak_tf, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak_tf, "traffic": None, "kernel": "contract_simt_kernel<double>",
+                "peak_source": fp64_how}
         dtype = "f64"
     elif args.precision == "fp64e":
-        c_ms = prof["contract_hi"][0] / steps
+        c_ms = prof["contract_hi"][0]
+        nlaunch = max(1, prof["contract_hi"][1])
         ach = flops_step / (c_ms / 1000.0) / 1e12
-        pk = bf / 15.0
-        nlaunch = max(1, prof["contract_hi"][1] // steps)
-        roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+        roof = {"bound": "tensor", "achieved": ach, "peak": bf, "unit": "TFLOP/s", "frac": ach / bf,
                 "traffic": (OZ_DRAM_BYTES_PER_G_ELEMENT * gelems_step / nlaunch
                             if OZ_DRAM_BYTES_PER_G_ELEMENT else None),
-                "traffic_note": "bytes per launch: dram read+write per G element of the ncu capture of "
-                                "oz_contract_kernel on CAS(6e,18o) x G elements per launch of this step",
-                "kernel": "oz_contract_kernel",
-                "peak_source": bf_src + " / 15 (15 FP16 slice products per FP64-accurate product; dense FP16 "
-                                        "runs at the BF16 rate)",
-                "executed_fp16_tflops": exec_step / (c_ms / 1000.0) / 1e12}
+                "kernel": "oz_contract_kernel", "peak_source": bf_src,
+                "achieved_note": "algorithmic FP64-equivalent FLOPs (2 ndet npair^2 per sigma) / event-timed "
+                                 "oz_contract_kernel time of one profiled step",
+                "launches_per_step": nlaunch,
+                "emulation": {"fp16_products_per_fp64_product": 15, "ceiling": bf / 15.0,
+                              "frac_of_ceiling": ach / (bf / 15.0),
+                              "executed_fp16_tflops": exec_step / (c_ms / 1000.0) / 1e12}}
         dtype = "f64 (FP16 tensor-core emulation)"
     else:
-        lo_ms = prof["contract"][0] / steps
-        hi_ms = prof["contract_hi"][0] / steps
+        lo_ms = prof["contract"][0]
+        hi_ms = prof["contract_hi"][0]
         ach = flops_step / ((lo_ms + hi_ms) / 1000.0) / 1e12
         roof = {"bound": "tensor", "achieved": ach, "peak": bf, "unit": "TFLOP/s", "frac": ach / bf,
                 "traffic": None, "kernel": "tc_contract_bf16_kernel + oz_contract_kernel", "peak_source": bf_src}
@@ -340,44 +399,66 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": dtype, "data": "synthetic",
-        "config": {"workload": "chain-24-uneven, iFCI to 3 bodies, 2324 CI problems, max CAS(6e,18o)",
-                   "seed": chain.seed, "bodies": chain.nbody, "orbitals": chain.norb,
-                   "max_order": args.max_order, "precision": args.precision,
-                   "davidson": {"r_tol": 1e-6, "e_tol": 1e-10, "max_space": 12},
-                   "l2": "inputs larger than L2: Davidson vectors of one step ~38 GB",
+        "config": {"workload": WORKLOAD_NAMES[args.workload], "seed": chain.seed, "bodies": chain.nbody,
+                   "orbitals": chain.norb, "max_order": args.max_order, "precision": args.precision,
+                   "davidson": dict(r_tol=R_TOL, e_tol=E_TOL, decouple_tol=1e-5, **tuned),
+                   "l2": "inputs larger than L2: Davidson vectors of one step are tens of GB",
                    "parallelism": f"{world} independent chains (one per GPU)"},
-        "sigma_tflops": flops_step / (sig_ms / 1000.0) / 1e12 if sig_ms > 0 else None,
-        "kernel_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
         "roofline": roof,
-        "class_rooflines": class_rooflines(subs, its, {k: v[0] for k, v in prof.items()}, steps,
-                                           float(peaks.get("hbm_gbs", 6800.0)), fp64_peak_tf),
+        "autotune": tune_info,
         "gpu_launches": int(launches),
         "clocks": clk,
         "e_total": out["e_total"],
+        "profiled_step": {"ms": sum(v[0] for v in prof.values()),
+                          "kernel_ms": {k: v[0] for k, v in prof.items()},
+                          "sigma_tflops": flops_step / (sig_ms / 1000.0) / 1e12 if sig_ms > 0 else None,
+                          "class_rooflines": class_rooflines(subs, its, {k: v[0] for k, v in prof.items()}, 1,
+                                                             float(peaks.get("hbm_gbs", 6800.0)), fp64_peak_tf),
+                          "e_total": outp["e_total"]},
     }
     if not args.no_compare and world == 1:
-        paths = {}
-        if args.precision != "fp64":
-            o64, ms64, _, _ = timed("fp64", 1, 0)
-            paths["fp64"] = {"value": nsub / (ms64 / 1000.0), "ms_per_step": ms64, "warmup": 0,
-                             "e_total": o64["e_total"]}
-            line["speedup_vs_fp64_path"] = value / paths["fp64"]["value"]
-            line["e_total_minus_fp64_path"] = out["e_total"] - o64["e_total"]
-        if args.precision != "bf16":
-            ob, msb, _, _ = timed("bf16", 1, 1)
-            paths["bf16_mixed"] = {"value": nsub / (msb / 1000.0), "ms_per_step": msb, "warmup": 1,
-                                   "e_total": ob["e_total"]}
-        line["other_paths"] = paths
+        line["paths_sample"] = paths_sample(ifci, torch, handle, chain, sysd, args, dev)
     if not args.no_e2e:
         line["e2e"] = _e2e(ifci, handle, chain, args.max_order, opts_for(args.precision), world, nsub, dist, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_baseline(workload(0), args.max_order, args.sample_seconds)
+        line["cpu_baseline"] = oracle_baseline(workload(0, args.workload), args.max_order, args.sample_seconds)
     handle.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def paths_sample(ifci, torch, handle, chain, sysd, args, dev):
+    """FP64E, plain FP64 and mixed BF16 (+FP64E restarts) on the same seeded
+    sample of body sets (their frozen-body CI problems through
+    ifci_davidson_batched, one batch per path): increments/s of each path and
+    the largest energy difference from the plain FP64 path."""
+    sample = compare_sample(chain, args.max_order, args.compare_fraction)
+    probs = []
+    for X, n, k in sample:
+        h1, eri, ec = ifci.ifci_frozen_core(handle, sysd, X)
+        probs.append(ifci.CIProblem(n, k, h1, eri, ec))
+    res = {}
+    for name, prec, hi in (("fp64e", "fp64e", "fp64e"), ("fp64", "fp64", "fp64"), ("bf16_mixed", "bf16", "fp64e")):
+        o = ifci.davidson_opts(prec, hi_precision=hi, r_tol=R_TOL, e_tol=E_TOL, max_iter=300)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e, it, st = ifci.ifci_davidson_batched(handle, probs, o, allow_unconverged=True)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        res[name] = {"increments_per_s": len(probs) / wall, "seconds": wall, "iters_mean": float(np.mean(it)),
+                     "unconverged": int(np.sum(st != 0)), "_e": e}
+    e64 = res["fp64"]["_e"]
+    for name in res:
+        d = res[name].pop("_e") - e64
+        res[name]["max_abs_minus_fp64_eh"] = float(np.max(np.abs(d)))
+        res[name]["speedup_vs_fp64"] = res[name]["increments_per_s"] / res["fp64"]["increments_per_s"]
+    nk = [sum(1 for s in sample if s[2] == k) for k in range(1, args.max_order + 1)]
+    return {"sample": f"{len(sample)} body sets ({' + '.join(map(str, nk))} of sizes 1..{args.max_order}; "
+                      f"a seeded {args.compare_fraction:.0%} of the largest), each path timed once, set-up included",
+            "r_tol": R_TOL, "runs": res}
 
 
 def class_rooflines(subs, iters, kernel_ms, steps, hbm_gbs, fp64_tflops, max_space=12):
@@ -510,11 +591,12 @@ def c2_case(args, torch, ifci):
 
 def c4_case(args, torch, ifci):
     """Production-scale 3-body iFCI of the 40-body uneven chain (seed 2310):
-    10,700 body sets up to CAS(6e,18o), one timed ifci_increments per
-    precision (FP64E, mixed BF16 + FP64E, plain FP64; no warm-up: each run
-    builds its own tables and plans), then the RDM backward of the FP64E run.
-    Prints E_total per path, its difference from the plain FP64 path and
-    increments/s."""
+    10,700 body sets up to CAS(6e,18o), one timed ifci_increments per path
+    (FP64E, mixed BF16 + FP64E, plain FP64; no warm-up: each run builds its
+    own tables and plans), then the RDM backward of the FP64E run.  Prints
+    E_total per path, its difference from the plain FP64 path, the largest
+    per-set energy difference, and increments/s; with ``--dump DIR`` the
+    per-set energies go to DIR/c4_<path>.npz."""
     from synth import chain_40_uneven
     dev = torch.device("cuda", 0)
     chain = chain_40_uneven()
@@ -522,17 +604,22 @@ def c4_case(args, torch, ifci):
                              torch.tensor(chain.eri_packed(), device=dev))
     nsub = len(subset_sizes(chain, 3))
     paths = [("fp64e", "fp64e", "fp64e"), ("bf16+fp64e", "bf16", "fp64e"), ("fp64", "fp64", "fp64")]
-    res = {}
+    res, ex = {}, {}
     with ifci.Handle(0, 0) as h:
         for name, prec, hi in paths:
-            opts = ifci.davidson_opts(prec, hi_precision=hi, r_tol=1e-7, e_tol=1e-11, max_iter=300)
+            opts = ifci.davidson_opts(prec, hi_precision=hi, r_tol=R_TOL, e_tol=E_TOL, max_iter=300)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            out = ifci.ifci_increments(h, sysd, 3, opts)
+            out = ifci.ifci_increments(h, sysd, 3, opts, allow_unconverged=True)
             torch.cuda.synchronize(dev)
             wall = time.perf_counter() - t0
+            ex[name] = out["e_x"]
             res[name] = {"e_total": out["e_total"], "seconds": wall, "increments_per_s": nsub / wall,
                          "unconverged": int(np.sum(out["status"] != 0)), "iters_mean": float(np.mean(out["iters"]))}
+            if args.dump:
+                os.makedirs(args.dump, exist_ok=True)
+                np.savez(os.path.join(args.dump, f"c4_{name}.npz"), e_x=out["e_x"], iters=out["iters"],
+                         status=out["status"], e0=out["e0"], e_total=out["e_total"])
             if name == "fp64e":
                 t0 = time.perf_counter()
                 dh, dV = ifci.ifci_rdm_backward(h, sysd, 3, 1.0, opts)
@@ -543,8 +630,10 @@ def c4_case(args, torch, ifci):
                 del dh, dV
     for name in res:
         res[name]["minus_fp64_eh"] = res[name]["e_total"] - res["fp64"]["e_total"]
-    print(json.dumps({"case": "c4", "workload": "chain-40-uneven (seed 2310), iFCI to 3 bodies, "
-                      f"{nsub} CI problems, max CAS(6e,18o)", "runs": res}), flush=True)
+        res[name]["max_set_minus_fp64_eh"] = float(np.max(np.abs(ex[name] - ex["fp64"])))
+        res[name]["speedup_vs_fp64"] = res[name]["increments_per_s"] / res["fp64"]["increments_per_s"]
+    print(json.dumps({"case": "c4", "workload": WORKLOAD_NAMES["c4"], "davidson": {"r_tol": R_TOL, "e_tol": E_TOL},
+                      "runs": res}), flush=True)
     return 0
 
 

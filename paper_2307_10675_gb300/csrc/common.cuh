@@ -136,6 +136,12 @@ struct DavArena {
 inline cudaStream_t as_cuda(ifci_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
 
 int device_sm_count(int device);
+// Grid of a grid-stride kernel over n blocks of work: at most per_sm
+// resident blocks per SM (at least 1 block).
+inline int stride_grid(int device, long long n, int per_sm) {
+    const long long g = (long long)device_sm_count(device) * per_sm;
+    return (int)(n < 1 ? 1 : (n < g ? n : g));
+}
 
 // The dynamic shared memory a kernel may use is a per-device attribute: each
 // caller keeps one of these per kernel and raises the attribute on a device

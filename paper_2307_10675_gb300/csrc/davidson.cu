@@ -70,8 +70,8 @@ __device__ void block_sum_store(double (&v)[NV], int nv, double *out) {
 // that gives the subspace a nonzero overlap with every state of the
 // spin-flip-even sector.
 
-__global__ void init_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st, int max_space) {
-    const DavProb p = probs[blockIdx.x];
+__device__ __forceinline__ void init_kernel_body(const DavProb *__restrict__ probs, DavState *__restrict__ st, int max_space, int w_) {
+    const DavProb p = probs[w_];
     __shared__ double bv[256];
     __shared__ long long bi[256];
     double best = 1e300;
@@ -116,7 +116,14 @@ __global__ void init_kernel(const DavProb *__restrict__ probs, DavState *__restr
         s.tgt = 0;
         for (int r = 0; r < kKeep; r++) s.rn[r] = 1e300;
         s.rebuild_to = nv + (ns >= 0 ? 1 : 0);   // sigmas of the start block, one per iteration
-        st[blockIdx.x] = s;
+        st[w_] = s;
+    }
+}
+
+__global__ void init_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st, int max_space, int nprob_) {
+    for (int w = blockIdx.x; w < nprob_; w += gridDim.x) {
+        init_kernel_body(probs, st, max_space, w);
+        __syncthreads();   // shared memory is reused by the next body
     }
 }
 
@@ -135,9 +142,9 @@ __device__ __forceinline__ double pair_noise(int a, int b) {
 // on the P-space determinants; a function of the global string pair, so it is
 // symmetric in a symmetric block).  A problem with a start vector of its own
 // copies it to slot 0.
-__global__ void __launch_bounds__(256) init_vec_kernel(const DavProb *__restrict__ probs,
-                                                       const WorkItem *__restrict__ items, int max_space) {
-    const WorkItem it = items[blockIdx.x];
+__device__ __forceinline__ void init_vec_kernel_body(const DavProb *__restrict__ probs,
+                                                       const WorkItem *__restrict__ items, int max_space, int w_) {
+    const WorkItem it = items[w_];
     const DavProb &p = probs[it.prob];
     int nv, ns;
     start_block(p.ndim, max_space, p.seed != nullptr, &nv, &ns);
@@ -155,12 +162,17 @@ __global__ void __launch_bounds__(256) init_vec_kernel(const DavProb *__restrict
     }
 }
 
+__global__ void __launch_bounds__(256) init_vec_kernel(const DavProb *__restrict__ probs,
+                                                       const WorkItem *__restrict__ items, int max_space, int nitem_) {
+    for (int w = blockIdx.x; w < nitem_; w += gridDim.x) init_vec_kernel_body(probs, items, max_space, w);
+}
+
 // normalise the noise slot of the start block (part: its |.|^2 per item)
-__global__ void __launch_bounds__(256) init_scale_kernel(const DavProb *__restrict__ probs,
+__device__ __forceinline__ void init_scale_kernel_body(const DavProb *__restrict__ probs,
                                                          const DavState *__restrict__ st,
                                                          const WorkItem *__restrict__ items,
-                                                         const double *__restrict__ part) {
-    const WorkItem it = items[blockIdx.x];
+                                                         const double *__restrict__ part, int w_) {
+    const WorkItem it = items[w_];
     const DavProb &p = probs[it.prob];
     const int ns = st[it.prob].noise_slot;
     if (ns < 0) return;
@@ -170,6 +182,13 @@ __global__ void __launch_bounds__(256) init_scale_kernel(const DavProb *__restri
     double *v = p.B + (long long)ns * p.ndet;
     long long end = min(it.start + (long long)kVecChunk, p.ndet);
     for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x) v[I] *= inv;
+}
+
+__global__ void __launch_bounds__(256) init_scale_kernel(const DavProb *__restrict__ probs,
+                                                         const DavState *__restrict__ st,
+                                                         const WorkItem *__restrict__ items,
+                                                         const double *__restrict__ part, int nitem_) {
+    for (int w = blockIdx.x; w < nitem_; w += gridDim.x) init_scale_kernel_body(probs, st, items, part, w);
 }
 
 // sigma selectors: the hi plan (FP64 or FP64-accurate) for exact problems, the
@@ -192,9 +211,9 @@ __global__ void select_kernel(const DavState *__restrict__ st, int nprob, int mi
 // ------------------------------------------------------------------ subspace
 
 // partial[item][j] = <b_j | sigma_new> over the item's determinants, j <= newest.
-__global__ void __launch_bounds__(256) dots_kernel(const DavProb *__restrict__ probs, const DavState *__restrict__ st,
-                                                   const WorkItem *__restrict__ items, double *__restrict__ part) {
-    const WorkItem it = items[blockIdx.x];
+__device__ __forceinline__ void dots_kernel_body(const DavProb *__restrict__ probs, const DavState *__restrict__ st,
+                                                   const WorkItem *__restrict__ items, double *__restrict__ part, int w_) {
+    const WorkItem it = items[w_];
     const DavState s = st[it.prob];
     if (!s.active) return;
     const DavProb &p = probs[it.prob];
@@ -210,7 +229,15 @@ __global__ void __launch_bounds__(256) dots_kernel(const DavProb *__restrict__ p
         for (int j = 0; j < kMaxSpace; j++)
             if (j < k) acc[j] += p.B[(long long)j * p.ndet + I] * sv;
     }
-    block_sum_store<kMaxSpace>(acc, k, part + (long long)blockIdx.x * kNP);
+    block_sum_store<kMaxSpace>(acc, k, part + (long long)w_ * kNP);
+}
+
+__global__ void __launch_bounds__(256) dots_kernel(const DavProb *__restrict__ probs, const DavState *__restrict__ st,
+                                                   const WorkItem *__restrict__ items, double *__restrict__ part, int nitem_) {
+    for (int w = blockIdx.x; w < nitem_; w += gridDim.x) {
+        dots_kernel_body(probs, st, items, part, w);
+        __syncthreads();   // shared memory is reused by the next body
+    }
 }
 
 // Cyclic Jacobi on a symmetric k x k matrix (k <= kMaxSpace): the nk <= k
@@ -271,9 +298,9 @@ __device__ void jacobi_lowest(double *A, double *V, int k, int nk, double *theta
 }
 
 // One block per problem: finish the subspace column and solve the projected problem.
-__global__ void solve_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st,
-                             const double *__restrict__ part, double *__restrict__ gs, double *__restrict__ ys) {
-    const int i = blockIdx.x;
+__device__ __forceinline__ void solve_kernel_body(const DavProb *__restrict__ probs, DavState *__restrict__ st,
+                             const double *__restrict__ part, double *__restrict__ gs, double *__restrict__ ys, int w_) {
+    const int i = w_;
     DavState s = st[i];
     if (!s.active) return;
     const DavProb p = probs[i];
@@ -307,14 +334,22 @@ __global__ void solve_kernel(const DavProb *__restrict__ probs, DavState *__rest
     }
 }
 
+__global__ void solve_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st,
+                             const double *__restrict__ part, double *__restrict__ gs, double *__restrict__ ys, int nprob_) {
+    for (int w = blockIdx.x; w < nprob_; w += gridDim.x) {
+        solve_kernel_body(probs, st, part, gs, ys, w);
+        __syncthreads();   // shared memory is reused by the next body
+    }
+}
+
 // For the targeted Ritz pair (theta, y): t = sum_j y_j (S_j - theta B_j);
 // ||t||^2; t /= (theta - H_II); dots <b_j|t>.
-__global__ void __launch_bounds__(256) residual_kernel(const DavProb *__restrict__ probs,
+__device__ __forceinline__ void residual_kernel_body(const DavProb *__restrict__ probs,
                                                        const DavState *__restrict__ st,
                                                        const WorkItem *__restrict__ items,
                                                        const double *__restrict__ ys, int max_space,
-                                                       double *__restrict__ part) {
-    const WorkItem it = items[blockIdx.x];
+                                                       double *__restrict__ part, int w_) {
+    const WorkItem it = items[w_];
     const DavState s = st[it.prob];
     if (!s.active) return;
     const DavProb &p = probs[it.prob];
@@ -365,16 +400,27 @@ __global__ void __launch_bounds__(256) residual_kernel(const DavProb *__restrict
     if (threadIdx.x < kMaxSpace + 2 && (threadIdx.x < k || threadIdx.x >= kMaxSpace)) {
         double v = 0.0;
         for (int w = 0; w < 8; w++) v += red[w][threadIdx.x];
-        part[(long long)blockIdx.x * kNP + threadIdx.x] = v;
+        part[(long long)w_ * kNP + threadIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) residual_kernel(const DavProb *__restrict__ probs,
+                                                       const DavState *__restrict__ st,
+                                                       const WorkItem *__restrict__ items,
+                                                       const double *__restrict__ ys, int max_space,
+                                                       double *__restrict__ part, int nitem_) {
+    for (int w = blockIdx.x; w < nitem_; w += gridDim.x) {
+        residual_kernel_body(probs, st, items, ys, max_space, part, w);
+        __syncthreads();   // shared memory is reused by the next body
     }
 }
 
 // Convergence test, restart decision, CGS coefficients.  One block per problem.
-__global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st,
+__device__ __forceinline__ void check_kernel_body(const DavProb *__restrict__ probs, DavState *__restrict__ st,
                              const double *__restrict__ part, double *__restrict__ coef, const double *__restrict__ ys,
                              double *__restrict__ gs, int max_space, int restart_at, int keep_max, int mixed,
-                             int max_iter, double e_tol, double r_tol, int *__restrict__ nactive) {
-    const int i = blockIdx.x;
+                             int max_iter, double e_tol, double r_tol, int *__restrict__ nactive, int w_) {
+    const int i = w_;
     DavState s = st[i];
     if (!s.active) return;
     const DavProb p = probs[i];
@@ -493,16 +539,26 @@ __global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__rest
     st[i] = s;
 }
 
+__global__ void check_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st,
+                             const double *__restrict__ part, double *__restrict__ coef, const double *__restrict__ ys,
+                             double *__restrict__ gs, int max_space, int restart_at, int keep_max, int mixed,
+                             int max_iter, double e_tol, double r_tol, int *__restrict__ nactive, int nprob_) {
+    for (int w = blockIdx.x; w < nprob_; w += gridDim.x) {
+        check_kernel_body(probs, st, part, coef, ys, gs, max_space, restart_at, keep_max, mixed, max_iter, e_tol, r_tol, nactive, w);
+        __syncthreads();   // shared memory is reused by the next body
+    }
+}
+
 // Restart: B_r <- sum_j Y_r[j] B_j and S_r <- sum_j Y_r[j] S_j for the kept
 // Ritz vectors r < nform; a thick restart (tslot >= 0) also moves the
 // correction from the scratch slot to slot nform, a phase switch of the mixed
 // mode (tslot < 0) drops it and rebuilds the S_r exactly.  Every old slot of
 // an element is read before any is written.
-__global__ void __launch_bounds__(256) restart_kernel(const DavProb *__restrict__ probs,
+__device__ __forceinline__ void restart_kernel_body(const DavProb *__restrict__ probs,
                                                       const DavState *__restrict__ st,
                                                       const WorkItem *__restrict__ items, const double *__restrict__ ys,
-                                                      int max_space, int mixed) {
-    const WorkItem it = items[blockIdx.x];
+                                                      int max_space, int mixed, int w_) {
+    const WorkItem it = items[w_];
     const DavState s = st[it.prob];
     if (!s.active || !s.restart) return;
     const DavProb &p = probs[it.prob];
@@ -536,12 +592,19 @@ __global__ void __launch_bounds__(256) restart_kernel(const DavProb *__restrict_
     }
 }
 
+__global__ void __launch_bounds__(256) restart_kernel(const DavProb *__restrict__ probs,
+                                                      const DavState *__restrict__ st,
+                                                      const WorkItem *__restrict__ items, const double *__restrict__ ys,
+                                                      int max_space, int mixed, int nitem_) {
+    for (int w = blockIdx.x; w < nitem_; w += gridDim.x) restart_kernel_body(probs, st, items, ys, max_space, mixed, w);
+}
+
 // t -= sum_{j<k} coef_j b_j ; then dots <b_j|t> and |t|^2 for the next pass.
-__global__ void __launch_bounds__(256) ortho_kernel(const DavProb *__restrict__ probs, const DavState *__restrict__ st,
+__device__ __forceinline__ void ortho_kernel_body(const DavProb *__restrict__ probs, const DavState *__restrict__ st,
                                                     const WorkItem *__restrict__ items,
                                                     const double *__restrict__ coef, int max_space,
-                                                    double *__restrict__ part, int pass) {
-    const WorkItem it = items[blockIdx.x];
+                                                    double *__restrict__ part, int pass, int w_) {
+    const WorkItem it = items[w_];
     const DavState s = st[it.prob];
     if (!s.active || s.tslot < 0) return;
     if (pass == 1 && s.skip2) return;
@@ -584,7 +647,17 @@ __global__ void __launch_bounds__(256) ortho_kernel(const DavProb *__restrict__ 
     if (threadIdx.x <= kMaxSpace && (threadIdx.x < k || threadIdx.x == kMaxSpace)) {
         double v = 0.0;
         for (int w = 0; w < 8; w++) v += red[w][threadIdx.x];
-        part[(long long)blockIdx.x * kNP + threadIdx.x] = v;
+        part[(long long)w_ * kNP + threadIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) ortho_kernel(const DavProb *__restrict__ probs, const DavState *__restrict__ st,
+                                                    const WorkItem *__restrict__ items,
+                                                    const double *__restrict__ coef, int max_space,
+                                                    double *__restrict__ part, int pass, int nitem_) {
+    for (int w = blockIdx.x; w < nitem_; w += gridDim.x) {
+        ortho_kernel_body(probs, st, items, coef, max_space, part, pass, w);
+        __syncthreads();   // shared memory is reused by the next body
     }
 }
 
@@ -592,9 +665,9 @@ __global__ void __launch_bounds__(256) ortho_kernel(const DavProb *__restrict__ 
 // The second pass runs only when the first one removed more than half of
 // |t|^2 (the DGKS criterion with eta = 1/sqrt 2: a first pass that kept
 // |t| >= |t_before| / sqrt 2 leaves t orthogonal to working precision).
-__global__ void reduce_coef_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st,
-                                   const double *__restrict__ part, double *__restrict__ coef, int pass) {
-    const int i = blockIdx.x;
+__device__ __forceinline__ void reduce_coef_kernel_body(const DavProb *__restrict__ probs, DavState *__restrict__ st,
+                                   const double *__restrict__ part, double *__restrict__ coef, int pass, int w_) {
+    const int i = w_;
     DavState s = st[i];
     if (!s.active || s.tslot < 0) return;
     if (pass == 1 && s.skip2) return;
@@ -613,13 +686,18 @@ __global__ void reduce_coef_kernel(const DavProb *__restrict__ probs, DavState *
     if (threadIdx.x > k && threadIdx.x < kMaxSpace) coef[(long long)i * kNP + threadIdx.x] = 0.0;
 }
 
+__global__ void reduce_coef_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st,
+                                   const double *__restrict__ part, double *__restrict__ coef, int pass, int nprob_) {
+    for (int w = blockIdx.x; w < nprob_; w += gridDim.x) reduce_coef_kernel_body(probs, st, part, coef, pass, w);
+}
+
 // b_k = t / |t|, symmetrised over (I_a, I_b) <-> (I_b, I_a) in a symmetric
 // block; the new slot becomes the next sigma target.  One thread per pair
 // (I, I^T) with I_a >= I_b (per element in an off-diagonal block).
-__global__ void __launch_bounds__(256) normalize_kernel(const DavProb *__restrict__ probs,
+__device__ __forceinline__ void normalize_kernel_body(const DavProb *__restrict__ probs,
                                                         const DavState *__restrict__ st,
-                                                        const WorkItem *__restrict__ items, int max_space) {
-    const WorkItem it = items[blockIdx.x];
+                                                        const WorkItem *__restrict__ items, int max_space, int w_) {
+    const WorkItem it = items[w_];
     const DavState s = st[it.prob];
     if (!s.active || s.tslot < 0) return;
     const DavProb &p = probs[it.prob];
@@ -644,6 +722,12 @@ __global__ void __launch_bounds__(256) normalize_kernel(const DavProb *__restric
         dst[I] = v;
         dst[It] = v;
     }
+}
+
+__global__ void __launch_bounds__(256) normalize_kernel(const DavProb *__restrict__ probs,
+                                                        const DavState *__restrict__ st,
+                                                        const WorkItem *__restrict__ items, int max_space, int nitem_) {
+    for (int w = blockIdx.x; w < nitem_; w += gridDim.x) normalize_kernel_body(probs, st, items, max_space, w);
 }
 
 __global__ void advance_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st, int nprob,
@@ -692,11 +776,11 @@ __global__ void advance_kernel(const DavProb *__restrict__ probs, DavState *__re
 }
 
 // c_out = sum_j y_j B_j for every finished problem that asked for it
-__global__ void __launch_bounds__(256) ritz_out_kernel(const DavProb *__restrict__ probs,
+__device__ __forceinline__ void ritz_out_kernel_body(const DavProb *__restrict__ probs,
                                                        const DavState *__restrict__ st,
                                                        const WorkItem *__restrict__ items,
-                                                       const double *__restrict__ ys) {
-    const WorkItem it = items[blockIdx.x];
+                                                       const double *__restrict__ ys, int w_) {
+    const WorkItem it = items[w_];
     const DavProb &p = probs[it.prob];
     if (!p.c_out) return;
     const DavState s = st[it.prob];
@@ -714,15 +798,23 @@ __global__ void __launch_bounds__(256) ritz_out_kernel(const DavProb *__restrict
     }
 }
 
+__global__ void __launch_bounds__(256) ritz_out_kernel(const DavProb *__restrict__ probs,
+                                                       const DavState *__restrict__ st,
+                                                       const WorkItem *__restrict__ items,
+                                                       const double *__restrict__ ys, int nitem_) {
+    for (int w = blockIdx.x; w < nitem_; w += gridDim.x) ritz_out_kernel_body(probs, st, items, ys, w);
+}
+
 // ------------------------------------------------------------------ driver
 
 int dav_init(ifci_handle_t h, DavBatch &b, const HdiagDesc *d_hd, cudaStream_t s) {
-    init_kernel<<<b.nprob, 256, 0, s>>>(b.d_probs, b.d_state, b.max_space);
+    const int nvi = (int)b.vitems.size();
+    init_kernel<<<stride_grid(h->device, b.nprob, 8), 256, 0, s>>>(b.d_probs, b.d_state, b.max_space, b.nprob);
     IFCI_LAUNCH_CHECK(h);
-    init_vec_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_vitems, b.max_space);
+    init_vec_kernel<<<stride_grid(h->device, nvi, 8), 256, 0, s>>>(b.d_probs, b.d_vitems, b.max_space, nvi);
     IFCI_LAUNCH_CHECK(h);
     IFCI_TRY(launch_pspace_start(h, b, d_hd, s));
-    init_scale_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);
+    init_scale_kernel<<<stride_grid(h->device, nvi, 8), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part, nvi);
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;
 }
@@ -731,6 +823,8 @@ int dav_init(ifci_handle_t h, DavBatch &b, const HdiagDesc *d_hd, cudaStream_t s
 static int dav_step(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_plan, int *d_hi, int *d_lo,
                     void *D, void *G, cudaStream_t s) {
     const int nitem = (int)b.vitems.size();
+    // grid-stride kernels: resident grids over the vector items and the problems
+    const int gi = stride_grid(h->device, nitem, 8), gp = stride_grid(h->device, b.nprob, 32);
     const bool mixed = lo_plan != nullptr;
     const int restart_at = b.max_space;
     select_kernel<<<(b.nprob + 127) / 128, 128, 0, s>>>(b.d_state, b.nprob, mixed ? 1 : 0, d_hi, d_lo);
@@ -752,27 +846,27 @@ static int dav_step(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan 
         IFCI_TRY(sector_move(false, d_lo));
     }
     ProfScope vec_scope(h, s, PK_VECTOR);
-    dots_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);
+    dots_kernel<<<gi, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part, nitem);
     IFCI_LAUNCH_CHECK(h);
-    solve_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_gs, b.d_y);
+    solve_kernel<<<gp, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_gs, b.d_y, b.nprob);
     IFCI_LAUNCH_CHECK(h);
-    residual_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, b.d_part);
+    residual_kernel<<<gi, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, b.d_part, nitem);
     IFCI_LAUNCH_CHECK(h);
     IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_nactive, 0, sizeof(int), s));
     // check_kernel records the subspace size before a restart (kold) for restart_kernel
-    check_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_coef, b.d_y, b.d_gs, b.max_space,
+    check_kernel<<<gp, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_coef, b.d_y, b.d_gs, b.max_space,
                                         restart_at, b.keep, mixed ? 1 : 0, b.max_iter, b.e_tol, b.r_tol,
-                                        b.d_nactive);
+                                        b.d_nactive, b.nprob);
     IFCI_LAUNCH_CHECK(h);
-    restart_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, mixed ? 1 : 0);
+    restart_kernel<<<gi, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, mixed ? 1 : 0, nitem);
     IFCI_LAUNCH_CHECK(h);
     for (int pass = 0; pass < 2; pass++) {
-        ortho_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_coef, b.max_space, b.d_part, pass);
+        ortho_kernel<<<gi, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_coef, b.max_space, b.d_part, pass, nitem);
         IFCI_LAUNCH_CHECK(h);
-        reduce_coef_kernel<<<b.nprob, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_coef, pass);
+        reduce_coef_kernel<<<gp, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_coef, pass, b.nprob);
         IFCI_LAUNCH_CHECK(h);
     }
-    normalize_kernel<<<nitem, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.max_space);
+    normalize_kernel<<<gi, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.max_space, nitem);
     IFCI_LAUNCH_CHECK(h);
     advance_kernel<<<(b.nprob + 127) / 128, 128, 0, s>>>(b.d_probs, b.d_state, b.nprob, b.r_tol, mixed ? 1 : 0);
     IFCI_LAUNCH_CHECK(h);
@@ -847,7 +941,7 @@ int dav_iterate(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan *lo_
         if (*h_nactive == 0) break;
     }
     if (st == IFCI_OK) {
-        ritz_out_kernel<<<nitem, 256, 0, ws>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y);
+        ritz_out_kernel<<<stride_grid(h->device, nitem, 8), 256, 0, ws>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, nitem);
         IFCI_LAUNCH_CHECK(h);
     }
     if (graph) {

@@ -78,6 +78,7 @@ constexpr int kYStride = kKeep * kNP;
 // vector that vanishes on the P-space determinants (exactly orthogonal to them)
 constexpr int kStartP = 3;
 constexpr int kPspMax = 64;
+constexpr int kPspBlock = 24;   // P-space of a block of a sectored space (the start of its own sector only)
 constexpr double kSectorWindow = 0.3;   // a second P-space block this close (Eh) gets its own pass
 // a sectored problem whose dropped integrals (H - H') are all below this
 // needs no polish with the full H: the energy changes at second order, ~1e-24

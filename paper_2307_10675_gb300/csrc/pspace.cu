@@ -110,9 +110,8 @@ __device__ double h_element(int n, const double *__restrict__ h1, const double *
 // Per problem: the kPsp lowest-diagonal canonical determinants (I_a <= I_b).
 // Each thread keeps its kSelPer lowest over a strided scan, then the block
 // sorts the candidates (bitonic, by value then index).
-__global__ void __launch_bounds__(kSelThreads)
-psp_select_kernel(const DavProb *__restrict__ probs, long long *__restrict__ pidx, int *__restrict__ pcount) {
-    const DavProb p = probs[blockIdx.x];
+__device__ __forceinline__ void psp_select_kernel_body(const DavProb *__restrict__ probs, long long *__restrict__ pidx, int *__restrict__ pcount, int w_) {
+    const DavProb p = probs[w_];
     __shared__ double sv[kSelCand];
     __shared__ long long si[kSelCand];
     double bv[kSelPer];
@@ -169,35 +168,42 @@ psp_select_kernel(const DavProb *__restrict__ probs, long long *__restrict__ pid
         }
     }
     const long long nsym = p.ndim;
-    const int P = nsym < kPsp ? (int)nsym : kPsp;
-    if (threadIdx.x < kPsp) pidx[blockIdx.x * kPsp + threadIdx.x] = threadIdx.x < P ? si[threadIdx.x] : -1;
-    if (threadIdx.x == 0) pcount[blockIdx.x] = P;
+    const int pmax = p.gc ? kPspBlock : kPsp;
+    const int P = nsym < pmax ? (int)nsym : pmax;
+    if (threadIdx.x < kPsp) pidx[w_ * kPsp + threadIdx.x] = threadIdx.x < P ? si[threadIdx.x] : -1;
+    if (threadIdx.x == 0) pcount[w_] = P;
+}
+
+__global__ void __launch_bounds__(kSelThreads) psp_select_kernel(const DavProb *__restrict__ probs, long long *__restrict__ pidx, int *__restrict__ pcount, int nprob_) {
+    for (int w = blockIdx.x; w < nprob_; w += gridDim.x) {
+        psp_select_kernel_body(probs, pidx, pcount, w);
+        __syncthreads();   // shared memory is reused by the next body
+    }
 }
 
 // Per problem (kPsp threads): H in the pair functions, its lowest eigenvectors
 // by cyclic Jacobi (rotations applied by all threads), written to the start
 // slots 0..nv-1; the random start vector is cleared on the P-space determinants.
-__global__ void __launch_bounds__(kPsp)
-psp_solve_kernel(const DavProb *__restrict__ probs, const HdiagDesc *__restrict__ hdd, const long long *__restrict__ pidx,
+__device__ __forceinline__ void psp_solve_kernel_body(const DavProb *__restrict__ probs, const HdiagDesc *__restrict__ hdd, const long long *__restrict__ pidx,
                  const int *__restrict__ pcount, const DavState *__restrict__ st, int max_space,
-                 double *__restrict__ blk_energy) {
+                 double *__restrict__ blk_energy, int w_) {
     extern __shared__ double psm[];
     double *A = psm;                       // [kPsp][kPsp]
     double *V = psm + kPsp * kPsp;         // [kPsp][kPsp]
     __shared__ double red[kPsp];
-    const DavProb p = probs[blockIdx.x];
-    const HdiagDesc d = hdd[blockIdx.x];
-    const int P = pcount[blockIdx.x];
+    const DavProb p = probs[w_];
+    const HdiagDesc d = hdd[w_];
+    const int P = pcount[w_];
     const int t = threadIdx.x;
     const int n = p.nb;
     const double rs2 = 0.7071067811865476;
     // row t of A: <u_t|H|u_c>, every term of the pair functions written out (in
     // an off-diagonal block, whose spin-flip image is not iterated, u_K = |K>)
     if (t < P) {
-        const long long K = pidx[blockIdx.x * kPsp + t];
+        const long long K = pidx[w_ * kPsp + t];
         const int ka = (int)(K / n), kb = (int)(K % n);
         for (int c = 0; c < P; c++) {
-            const long long L = pidx[blockIdx.x * kPsp + c];
+            const long long L = pidx[w_ * kPsp + c];
             const int la = (int)(L / n), lb = (int)(L % n);
             const int nbra = (ka == kb || !p.sym) ? 1 : 2, nket = (la == lb || !p.sym) ? 1 : 2;
             const double f = (nbra == 2 ? rs2 : 1.0) * (nket == 2 ? rs2 : 1.0);
@@ -315,8 +321,8 @@ psp_solve_kernel(const DavProb *__restrict__ probs, const HdiagDesc *__restrict_
             if (opens) first[nb++] = r;
         }
         if (blk_energy) {
-            blk_energy[2 * blockIdx.x] = A[order[first[0]] * kPsp + order[first[0]]];
-            blk_energy[2 * blockIdx.x + 1] = nb > 1 ? A[order[first[1]] * kPsp + order[first[1]]] : 1e300;
+            blk_energy[2 * w_] = A[order[first[0]] * kPsp + order[first[0]]];
+            blk_energy[2 * w_ + 1] = nb > 1 ? A[order[first[1]] * kPsp + order[first[1]]] : 1e300;
         }
         bool taken[kPsp];
         for (int r = 0; r < P; r++) taken[r] = false;
@@ -352,7 +358,7 @@ psp_solve_kernel(const DavProb *__restrict__ probs, const HdiagDesc *__restrict_
     }
     __syncthreads();
     if (t < P) {
-        const long long K = pidx[blockIdx.x * kPsp + t];
+        const long long K = pidx[w_ * kPsp + t];
         const int ka = (int)(K / n), kb = (int)(K % n);
         const long long KT = (long long)kb * n + ka;
         for (int r = 0; r < nv; r++) {
@@ -377,11 +383,20 @@ psp_solve_kernel(const DavProb *__restrict__ probs, const HdiagDesc *__restrict_
     }
 }
 
+__global__ void __launch_bounds__(kPsp) psp_solve_kernel(const DavProb *__restrict__ probs, const HdiagDesc *__restrict__ hdd, const long long *__restrict__ pidx,
+                 const int *__restrict__ pcount, const DavState *__restrict__ st, int max_space,
+                 double *__restrict__ blk_energy, int nprob_) {
+    for (int w = blockIdx.x; w < nprob_; w += gridDim.x) {
+        psp_solve_kernel_body(probs, hdd, pidx, pcount, st, max_space, blk_energy, w);
+        __syncthreads();   // shared memory is reused by the next body
+    }
+}
+
 // partial |.|^2 of the random start vector per vector work item
-__global__ void __launch_bounds__(256) norm_part_kernel(const DavProb *__restrict__ probs,
+__device__ __forceinline__ void norm_part_kernel_body(const DavProb *__restrict__ probs,
                                                         const DavState *__restrict__ st,
-                                                        const WorkItem *__restrict__ items, double *__restrict__ part) {
-    const WorkItem it = items[blockIdx.x];
+                                                        const WorkItem *__restrict__ items, double *__restrict__ part, int w_) {
+    const WorkItem it = items[w_];
     const DavProb &p = probs[it.prob];
     const int ns = st[it.prob].noise_slot;
     double acc = 0.0;
@@ -397,7 +412,16 @@ __global__ void __launch_bounds__(256) norm_part_kernel(const DavProb *__restric
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int i = 0; i < 8; i++) s += red[i];
-        part[(long long)blockIdx.x * kNP] = s;
+        part[(long long)w_ * kNP] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256) norm_part_kernel(const DavProb *__restrict__ probs,
+                                                        const DavState *__restrict__ st,
+                                                        const WorkItem *__restrict__ items, double *__restrict__ part, int nitem_) {
+    for (int w = blockIdx.x; w < nitem_; w += gridDim.x) {
+        norm_part_kernel_body(probs, st, items, part, w);
+        __syncthreads();   // shared memory is reused by the next body
     }
 }
 
@@ -426,15 +450,15 @@ int launch_pspace_start(ifci_handle_t h, const DavBatch &b, const HdiagDesc *d_h
     long long *pidx = b.d_pidx;
     int *pcount = b.d_pcount;
     if (!pidx || !pcount) return set_error(h, IFCI_ERR_OOM, "davidson: workspace (P-space)");
-    psp_select_kernel<<<b.nprob, kSelThreads, 0, s>>>(b.d_probs, pidx, pcount);
+    psp_select_kernel<<<stride_grid(h->device, b.nprob, 8), kSelThreads, 0, s>>>(b.d_probs, pidx, pcount, b.nprob);
     IFCI_LAUNCH_CHECK(h);
     const int smem = 2 * kPsp * kPsp * (int)sizeof(double);   // 64 KB
     static SmemOptIn opt;
     IFCI_CUDA_TRY(h, ensure_smem(opt, h->device, psp_solve_kernel, smem));
-    psp_solve_kernel<<<b.nprob, kPsp, smem, s>>>(b.d_probs, d_hd, pidx, pcount, b.d_state, b.max_space,
-                                                  b.d_blk_energy);
+    psp_solve_kernel<<<stride_grid(h->device, b.nprob, 3), kPsp, smem, s>>>(b.d_probs, d_hd, pidx, pcount, b.d_state, b.max_space,
+                                                  b.d_blk_energy, b.nprob);
     IFCI_LAUNCH_CHECK(h);
-    norm_part_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part);
+    norm_part_kernel<<<stride_grid(h->device, (long long)b.vitems.size(), 8), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part, (int)b.vitems.size());
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;
 }

@@ -94,11 +94,11 @@ __global__ void __launch_bounds__(256) mask_kernel(const MaskDesc *__restrict__ 
 // whole-space input of a sector unit's sigma: every block problem writes its
 // newest vector (zero if the flag says it takes no sigma this time) at its
 // determinants and, for an off-diagonal block, at their spin-flip images
-__global__ void __launch_bounds__(256) sector_gather_kernel(const DavProb *__restrict__ probs,
+__device__ __forceinline__ void sector_gather_kernel_body(const DavProb *__restrict__ probs,
                                                             const DavState *__restrict__ st,
                                                             const WorkItem *__restrict__ items,
-                                                            const int *__restrict__ flag) {
-    const WorkItem it = items[blockIdx.x];
+                                                            const int *__restrict__ flag, int w_) {
+    const WorkItem it = items[w_];
     const DavProb &p = probs[it.prob];
     if (!p.gc) return;
     const bool on = flag[it.prob] != 0;
@@ -114,12 +114,19 @@ __global__ void __launch_bounds__(256) sector_gather_kernel(const DavProb *__res
     }
 }
 
+__global__ void __launch_bounds__(256) sector_gather_kernel(const DavProb *__restrict__ probs,
+                                                            const DavState *__restrict__ st,
+                                                            const WorkItem *__restrict__ items,
+                                                            const int *__restrict__ flag, int nitem_) {
+    for (int w = blockIdx.x; w < nitem_; w += gridDim.x) sector_gather_kernel_body(probs, st, items, flag, w);
+}
+
 // each block problem takes its part of the whole-space sigma
-__global__ void __launch_bounds__(256) sector_scatter_kernel(const DavProb *__restrict__ probs,
+__device__ __forceinline__ void sector_scatter_kernel_body(const DavProb *__restrict__ probs,
                                                              const DavState *__restrict__ st,
                                                              const WorkItem *__restrict__ items,
-                                                             const int *__restrict__ flag) {
-    const WorkItem it = items[blockIdx.x];
+                                                             const int *__restrict__ flag, int w_) {
+    const WorkItem it = items[w_];
     const DavProb &p = probs[it.prob];
     if (!p.gc || !flag[it.prob]) return;
     double *y = p.S + (long long)st[it.prob].newest * p.ndet;
@@ -131,10 +138,17 @@ __global__ void __launch_bounds__(256) sector_scatter_kernel(const DavProb *__re
     }
 }
 
+__global__ void __launch_bounds__(256) sector_scatter_kernel(const DavProb *__restrict__ probs,
+                                                             const DavState *__restrict__ st,
+                                                             const WorkItem *__restrict__ items,
+                                                             const int *__restrict__ flag, int nitem_) {
+    for (int w = blockIdx.x; w < nitem_; w += gridDim.x) sector_scatter_kernel_body(probs, st, items, flag, w);
+}
+
 // diagonal of a block problem from its unit's whole-space diagonal (in gs)
-__global__ void __launch_bounds__(256) sector_hd_kernel(const DavProb *__restrict__ probs,
-                                                        const WorkItem *__restrict__ items) {
-    const WorkItem it = items[blockIdx.x];
+__device__ __forceinline__ void sector_hd_kernel_body(const DavProb *__restrict__ probs,
+                                                        const WorkItem *__restrict__ items, int w_) {
+    const WorkItem it = items[w_];
     const DavProb &p = probs[it.prob];
     if (!p.gc) return;
     double *hd = const_cast<double *>(p.hd);
@@ -144,6 +158,11 @@ __global__ void __launch_bounds__(256) sector_hd_kernel(const DavProb *__restric
         const int ia = (int)(I / p.nb), ib = (int)(I % p.nb);
         hd[I] = p.gs[(long long)blk_row(p, ia) * n + blk_col(p, ib)];
     }
+}
+
+__global__ void __launch_bounds__(256) sector_hd_kernel(const DavProb *__restrict__ probs,
+                                                        const WorkItem *__restrict__ items, int nitem_) {
+    for (int w = blockIdx.x; w < nitem_; w += gridDim.x) sector_hd_kernel_body(probs, items, w);
 }
 
 // a unit's sigma runs (per precision) when any of its problems asks for it
@@ -164,10 +183,10 @@ __global__ void unit_flags_kernel(const int2 *__restrict__ range, int nunit, con
 // the whole-space vector of a block's converged vector (c_out of the block
 // problem): x at the block's determinants, and at their spin-flip images for
 // an off-diagonal block (both scaled by 1/sqrt 2, so the result has unit norm)
-__global__ void __launch_bounds__(256) sector_expand_kernel(const DavProb *__restrict__ probs,
+__device__ __forceinline__ void sector_expand_kernel_body(const DavProb *__restrict__ probs,
                                                             const WorkItem *__restrict__ items,
-                                                            double *const *__restrict__ dst) {
-    const WorkItem it = items[blockIdx.x];
+                                                            double *const *__restrict__ dst, int w_) {
+    const WorkItem it = items[w_];
     const DavProb &p = probs[it.prob];
     double *out = dst[it.prob];
     if (!out || !p.c_out) return;
@@ -181,6 +200,12 @@ __global__ void __launch_bounds__(256) sector_expand_kernel(const DavProb *__res
         out[ga * n + gb] = v;
         if (!p.sym) out[gb * n + ga] = v;
     }
+}
+
+__global__ void __launch_bounds__(256) sector_expand_kernel(const DavProb *__restrict__ probs,
+                                                            const WorkItem *__restrict__ items,
+                                                            double *const *__restrict__ dst, int nitem_) {
+    for (int w = blockIdx.x; w < nitem_; w += gridDim.x) sector_expand_kernel_body(probs, items, dst, w);
 }
 
 }  // namespace
@@ -198,19 +223,19 @@ int launch_mask(ifci_handle_t h, int nprob, const MaskDesc *d_desc, cudaStream_t
 }
 
 int launch_sector_gather(ifci_handle_t h, const DavBatch &b, const int *flag, cudaStream_t s) {
-    sector_gather_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, flag);
+    sector_gather_kernel<<<stride_grid(h->device, (long long)b.vitems.size(), 8), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, flag, (int)b.vitems.size());
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;
 }
 
 int launch_sector_scatter(ifci_handle_t h, const DavBatch &b, const int *flag, cudaStream_t s) {
-    sector_scatter_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, flag);
+    sector_scatter_kernel<<<stride_grid(h->device, (long long)b.vitems.size(), 8), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, flag, (int)b.vitems.size());
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;
 }
 
 int launch_sector_hd(ifci_handle_t h, const DavBatch &b, cudaStream_t s) {
-    sector_hd_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_vitems);
+    sector_hd_kernel<<<stride_grid(h->device, (long long)b.vitems.size(), 8), 256, 0, s>>>(b.d_probs, b.d_vitems, (int)b.vitems.size());
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;
 }
@@ -222,7 +247,7 @@ int launch_unit_flags(ifci_handle_t h, const DavBatch &b, const int *hi, const i
 }
 
 int launch_sector_expand(ifci_handle_t h, const DavBatch &b, double *const *d_dst, cudaStream_t s) {
-    sector_expand_kernel<<<(int)b.vitems.size(), 256, 0, s>>>(b.d_probs, b.d_vitems, d_dst);
+    sector_expand_kernel<<<stride_grid(h->device, (long long)b.vitems.size(), 8), 256, 0, s>>>(b.d_probs, b.d_vitems, d_dst, (int)b.vitems.size());
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;
 }

@@ -41,9 +41,9 @@ def test_two_rank_weak_scaling_host_path():
         out = m.dict()
         mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
-    assert res[0][0] != res[1][0]                      # independent chains (seed 2308 + rank)
+    assert res[0][0] != res[1][0]                      # independent chains (seed 2310 + rank)
     assert res[0][1] == res[1][1]                      # same shape: same work per rank
-    assert res[0][3] == res[1][3] == 24 + 276 + 2024   # same CI problem count per rank
+    assert res[0][3] == res[1][3] == 40 + 780 + 9880   # same CI problem count per rank
     assert res[0][2] == res[1][2] == pytest.approx(107.0)   # every rank reports the slowest rank's time
 
 
