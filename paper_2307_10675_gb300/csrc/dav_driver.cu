@@ -41,6 +41,8 @@ struct Unit {
     const double *seed;      // start vector of the whole space, or nullptr
     int prob0, nprob;
     double *expand_to;       // sectored unit: whole-space target of the lowest block's vector, or nullptr
+    std::vector<int> label;  // sectored unit: group of each orbital (its FP64E contraction runs over the
+                             // pairs within one group only: H' has no other integrals)
 };
 
 // Counts (count = true) or takes (count = false) workspace pieces in one order.
@@ -140,9 +142,27 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
         hi.probs.push_back(sp);
         lop.probs.push_back(sp);
     }
+    // FP64E contraction of a sectored unit over its intra-group pairs
+    std::vector<std::vector<int32_t>> act(nu);
+    std::vector<std::vector<uint8_t>> pact(nu);
+    for (int u = 0; u < nu; u++) {
+        const Unit &U = units[u];
+        if (!oz || !U.sector || U.label.empty() || !hi.probs[u].sym) continue;
+        const int n = U.spec.n, np = n * (n + 1) / 2;
+        pact[u].assign(np, 0);
+        for (int P = 0; P < n; P++)
+            for (int Q = 0; Q <= P; Q++)
+                if (U.label[P] == U.label[Q]) {
+                    act[u].push_back(P * (P + 1) / 2 + Q);
+                    pact[u][P * (P + 1) / 2 + Q] = 1;
+                }
+        hi.probs[u].npc = (int)act[u].size();
+    }
     long long budget = o.det_budget > 0 ? o.det_budget : (1ll << 31);   // two 16 GB intermediates
     budget = std::max(budget, max_pd);
     budget = std::min(budget, std::max(sum_pd, max_pd));
+    for (int u = 0; u < nu; u++)   // placeholder until the device copy exists: plan_sigma tiles over npc
+        if (!act[u].empty()) hi.probs[u].act = act[u].data();
     IFCI_TRY(plan_sigma(h, hi, budget, hi_prec));
     if (lo) IFCI_TRY(plan_sigma(h, lop, budget * 8 / (long long)sigma_elem_bytes(o.precision), o.precision));
 
@@ -157,6 +177,8 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
         std::vector<void *> Wtc;
         std::vector<char *> Woz;
         std::vector<double *> hd, B, S, cblk;
+        std::vector<int32_t *> act, pmapc;
+        std::vector<uint8_t *> pact;
         int *sidx = nullptr;
         DavProb *probs = nullptr;
         DavState *state = nullptr;
@@ -188,6 +210,14 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
             // Davidson vectors are spin-flip symmetric: the tensor-core sigmas use
             // the alpha-only gathers where the pair map's offsets fit in int32
             if ((tc || oz) && 2ll * nstr * nstr < (1ll << 31)) m.pm[k] = c.take<int32_t>((size_t)nstr * pmap_ld(np));
+        }
+        m.act.assign(nu, nullptr); m.pmapc.assign(nu, nullptr); m.pact.assign(nu, nullptr);
+        for (int u = 0; u < nu; u++) {
+            if (act[u].empty()) continue;
+            const int nstr = (int)binom(units[u].spec.n, units[u].spec.m);
+            m.act[u] = c.take<int32_t>(act[u].size());
+            m.pact[u] = c.take<uint8_t>(pact[u].size());
+            m.pmapc[u] = c.take<int32_t>((size_t)nstr * pmap_ld((int)act[u].size()));
         }
         m.W.resize(nu); m.Wf.assign(nu, nullptr); m.Wtc.assign(nu, nullptr); m.Woz.assign(nu, nullptr);
         m.gc.assign(nu, nullptr); m.gs.assign(nu, nullptr);
@@ -300,6 +330,16 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
                 sp.sslot = &mem.state[U.prob0].newest;
             }
             sp.active = (pl == &hi ? mem.uhi : mem.ulo) + u;
+            if (pl == &hi && mem.act[u]) {
+                sp.act = mem.act[u];
+                sp.pact = mem.pact[u];
+                sp.pmapc = mem.pmapc[u];
+            } else {
+                sp.act = nullptr;
+                sp.pact = nullptr;
+                sp.pmapc = nullptr;
+                sp.npc = sp.np;
+            }
         }
     }
     for (int i = 0; i < n; i++) {
@@ -364,6 +404,14 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
                                      cudaMemcpyHostToDevice, s));
     IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_gs, 0, (size_t)n * kMaxSpace * kMaxSpace * 8, s));
     IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_y, 0, (size_t)n * kYStride * 8, s));
+    for (int u = 0; u < nu; u++) {
+        if (!mem.act[u]) continue;
+        const int k = cls[{units[u].spec.n, units[u].spec.m}];
+        const int nstr = (int)binom(units[u].spec.n, units[u].spec.m), np = units[u].spec.n * (units[u].spec.n + 1) / 2;
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.act[u], act[u].data(), act[u].size() * 4, cudaMemcpyHostToDevice, s));
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.pact[u], pact[u].data(), pact[u].size(), cudaMemcpyHostToDevice, s));
+        IFCI_TRY(launch_compact_pair_map(h, nstr, np, mem.pm[k], (int)act[u].size(), mem.act[u], mem.pmapc[u], s));
+    }
     int maxnp = 0;
     for (const Unit &U : units) maxnp = std::max(maxnp, U.spec.n * (U.spec.n + 1) / 2);
     IFCI_TRY(launch_fold(h, nu, mem.fold, maxnp, s));
@@ -562,6 +610,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
             }
             units[i].h1 = d.h1m;
             units[i].eri = d.erim;
+            units[i].label = label[i];
             md.push_back(d);
         }
         auto *d_md = reinterpret_cast<MaskDesc *>(q);

@@ -215,15 +215,18 @@ scatter_fixed_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__rest
     const int32_t *__restrict__ ea = p.exc + (size_t)ia * nexc;
     const int32_t *__restrict__ eb = p.exc + (size_t)ib * nexc;
     const long long *__restrict__ Gp = G + p.doff;
+    const uint8_t *__restrict__ pact = p.pact;   // G rows of other pairs are not written (their W is zero)
     long long acc = 0;
     for (int e = 0; e < nexc; e++) {
         const int32_t x = ea[e];
+        if (pact && !pact[exc_pair(x)]) continue;
         const long long gv = Gp[(long long)exc_pair(x) * ndet + (long long)exc_J(x) * nstr + ib];
         acc += (x & 1) ? -gv : gv;
     }
     const long long rowb = (long long)ia * nstr;
     for (int e = 0; e < nexc; e++) {
         const int32_t x = eb[e];
+        if (pact && !pact[exc_pair(x)]) continue;
         const long long gv = Gp[(long long)exc_pair(x) * ndet + rowb + exc_J(x)];
         acc += (x & 1) ? -gv : gv;
     }
@@ -268,7 +271,8 @@ int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision
         } else if (precision == IFCI_FP64E) {
             // one tile = up to 128 determinants x oz_tile_n() output pairs (sigma_oz.cu);
             // the output-pair tiles of a problem run back to back so W stays resident longer
-            for (int n0 = 0; n0 < p.np; n0 += oz_tile_n()) {
+            if (p.npc <= 0 || !p.act) p.npc = p.np;
+            for (int n0 = 0; n0 < p.npc; n0 += oz_tile_n()) {
                 size_t before = plan.tctiles.size();
                 tcg::append_row_tiles(plan.tctiles, (int)i, n0, p.nstr);
                 w.ntc += (int)(plan.tctiles.size() - before);

@@ -30,6 +30,15 @@ struct SigmaProb {
     const int *sslot;        // device slot index or nullptr (= 0)
     const int *active;       // device flag or nullptr (= active)
     long long doff;          // element offset of this problem's D and G blocks in a wave
+    // FP64-emulating contraction over a subset of the pairs (a sectored space,
+    // whose H' has no integral joining two groups): npc pairs act[0..npc) in
+    // ascending order, the pair map restricted to them (pmapc, rows of
+    // pmap_ld(npc)), and a flag per pair (pact) for the scatter, which skips
+    // the G rows of the other pairs.  act = nullptr: every pair (npc = np).
+    int npc;
+    const int32_t *act;
+    const int32_t *pmapc;
+    const uint8_t *pact;
 };
 
 // D/G elements one problem takes in a wave (the quantised +-c copies of the

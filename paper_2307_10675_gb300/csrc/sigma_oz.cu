@@ -84,7 +84,7 @@ __device__ __forceinline__ uint32_t digit_pair_f16(uint32_t a, uint32_t b, int D
 __device__ __forceinline__ const uint8_t *stage_src(const SigmaProb *probs, const WorkItem *tiles, int t, int a) {
     const WorkItem tile = tiles[t];
     const SigmaProb &p = probs[tile.prob];
-    const int KA = k_atoms(p.np), nt = tile.sub / kNT;
+    const int KA = k_atoms(p.act ? p.npc : p.np), nt = tile.sub / kNT;
     return (const uint8_t *)p.Woz + ((size_t)nt * KA + a) * kWStage;
 }
 
@@ -139,9 +139,11 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
         // descriptor fields in registers (the asm memory clobbers below would
         // otherwise make the compiler reload them from global memory)
         const SigmaProb &pg = probs[tile.prob];
-        const int np = pg.np, nstr = pg.nstr, sym = pg.sym;
+        // np: the pairs contracted (a sectored space: its active pairs, in compact order)
+        const int np = pg.act ? pg.npc : pg.np, nstr = pg.nstr, sym = pg.sym;
         const long long ndet = pg.ndet, doff = pg.doff;
-        const int32_t *pmap = pg.pmap;
+        const int32_t *pmap = pg.act ? pg.pmapc : pg.pmap;
+        const int32_t *act = pg.act;
         const long long *C = Q + pg.qoff;   // round(c 2^38 / dscale) (and its negation when sym)
         const int KA = k_atoms(np), n0 = tile.sub;
         const int Nt = round_up(min(kNT, np - n0), 16);
@@ -261,7 +263,7 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
                     const int A = n0 + c0 + j;
-                    if (c0 + j < Nt && A < np) Gp[(long long)A * ndet + K] = gi[j];
+                    if (c0 + j < Nt && A < np) Gp[(long long)(act ? act[A] : A) * ndet + K] = gi[j];
                 }
             }
         }
@@ -284,12 +286,16 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
 // 16-byte chunk c of a row at c ^ (row % 8), zeros beyond npair.
 __global__ void oz_pack_w_kernel(const SigmaProb *__restrict__ probs) {
     const SigmaProb &p = probs[blockIdx.x];
-    const int np = p.np, KA = k_atoms(np), NTl = n_tiles(np);
+    // a sectored space packs only its active pairs, in compact order
+    const int np = p.act ? p.npc : p.np, KA = k_atoms(np), NTl = n_tiles(np);
+    const int32_t *act = p.act;
     uint8_t *img = (uint8_t *)const_cast<void *>(p.Woz);
     __shared__ double red[256];
     double mx = 0.0;
-    for (long long i = threadIdx.x; i < (long long)np * np; i += blockDim.x)
-        mx = fmax(mx, fabs(p.W[(i / np) * p.ld + i % np]));
+    for (long long i = threadIdx.x; i < (long long)np * np; i += blockDim.x) {
+        const long long r = i / np, c = i % np;
+        mx = fmax(mx, fabs(p.W[(act ? act[r] : r) * (long long)p.ld + (act ? act[c] : c)]));
+    }
     red[threadIdx.x] = mx;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -307,7 +313,8 @@ __global__ void oz_pack_w_kernel(const SigmaProb *__restrict__ probs) {
         float sl[8][kS];
         for (int e2 = 0; e2 < 8; e2++) {
             const int k = a * 64 + ch * 8 + e2;
-            double x = (n < np && k < np) ? p.W[(long long)n * p.ld + k] / scale : 0.0;
+            double x = (n < np && k < np) ? p.W[(long long)(act ? act[n] : n) * p.ld + (act ? act[k] : k)] / scale
+                                          : 0.0;
             slice5(x, sl[e2]);
         }
         for (int i = 0; i < kS; i++) {
@@ -367,7 +374,7 @@ int launch_oz_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &
                        cudaStream_t s) {
     if (w.ntc == 0) return IFCI_OK;
     for (const SigmaProb &p : plan.probs)
-        if (p.np > kMaxNpExact)
+        if ((p.act ? p.npc : p.np) > kMaxNpExact)
             return set_error(h, IFCI_ERR_UNSUPPORTED, "FP64E: npair %d > %d (exact level sums)", p.np, kMaxNpExact);
     if (!h->d_err || !h->d_counter) return set_error(h, IFCI_ERR_INVALID_ARG, "FP64E: no error flag / counter");
     const size_t smem = 1024 + 2 * kWStage + kAStage;   // 205,824 B

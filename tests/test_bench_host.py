@@ -35,3 +35,17 @@ def test_class_rooflines_fields_and_scaling():
     assert math.isclose(out2["scatter"]["achieved"] * 2, out["scatter"]["achieved"])
     assert math.isclose(out2["davidson_vectors"]["achieved"] * 2, v["achieved"])
     assert bench.class_rooflines(subs, iters, {}, 1, 6791.4, 1.10) == {}
+
+
+def test_contracted_pairs_of_decoupled_groups():
+    """Three bodies far apart contract only their own pairs; three adjacent
+    bodies contract every pair of their union."""
+    from synth import chain_40_uneven
+    c = chain_40_uneven()
+    C = bench.body_coupling(c)
+    s = c.body_sizes
+    far = (0, 19, 39)
+    assert bench.contracted_pairs(far, s, C) == sum(s[b] * (s[b] + 1) // 2 for b in far)
+    near = (10, 11, 12)
+    n = sum(s[b] for b in near)
+    assert bench.contracted_pairs(near, s, C) == n * (n + 1) // 2
