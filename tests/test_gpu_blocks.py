@@ -110,7 +110,7 @@ def test_weakly_coupled_and_cas6e18o_sets_against_the_oracle(prec, hi, tol):
     chain = chain_40_uneven()
     gold = json.load(open(os.path.join(GOLDEN, "chain40_sectors_oracle.json")))["energies"]
     sets = [tuple(int(v) for v in k.split(",")) for k in gold]
-    assert len(sets) >= 12
+    assert len(sets) >= 18 and sum(gold[k]["ndet"] == 665856 for k in gold) >= 5
     opts = ifci.davidson_opts(prec, hi_precision=hi, r_tol=1e-7, e_tol=1e-11, max_iter=300)
     with ifci.Handle(0, 0) as h:
         e, st = _solve_sets(h, chain, sets, opts)
