@@ -240,106 +240,125 @@ __global__ void __launch_bounds__(256) dots_kernel(const DavProb *__restrict__ p
     }
 }
 
-// Cyclic Jacobi on a symmetric k x k matrix (k <= kMaxSpace): the nk <= k
-// lowest eigenpairs, theta[r] and y[r * kMaxSpace + i].
-__device__ void jacobi_lowest(double *A, double *V, int k, int nk, double *theta, double *y) {
-    for (int i = 0; i < k; i++)
-        for (int j = 0; j < k; j++) V[i * kMaxSpace + j] = (i == j) ? 1.0 : 0.0;
+// Cyclic Jacobi on the symmetric k x k matrix A (shared memory, row stride
+// kSolveLd) by one warp: every lane derives the same rotation from the
+// settled entries, then lane r rotates row r / column r (columns, rows and V
+// in turn, as the serial sweep does, so the arithmetic per element is the
+// same).  A sweep ends the iteration once the off-diagonal part is below
+// 1e-26 of |A|_F^2 (eigenvalue errors ~1e-26 |A| / gap); a rotation whose
+// A_pq is below 1e-18 (|A_pp| + |A_qq|) only sets A_pq = A_qp = 0.
+constexpr int kSolveLd = kMaxSpace + 1;
+constexpr int kSolveWarps = 4;
+
+__device__ void jacobi_warp(double *A, double *V, int k, int lane) {
+    if (lane < k)
+        for (int j = 0; j < k; j++) V[lane * kSolveLd + j] = lane == j ? 1.0 : 0.0;
+    __syncwarp();
     for (int sweep = 0; sweep < 60; sweep++) {
         double off = 0.0, tot = 0.0;
-        for (int i = 0; i < k; i++)
+        if (lane < k)
             for (int j = 0; j < k; j++) {
-                double a = A[i * kMaxSpace + j];
+                const double a = A[lane * kSolveLd + j];
                 tot += a * a;
-                if (i != j) off += a * a;
+                if (j != lane) off += a * a;
             }
-        if (off <= 1e-30 * tot || off == 0.0) break;
+        off = warp_sum(off);
+        tot = warp_sum(tot);
+        if (off <= 1e-26 * tot || off == 0.0) break;
         for (int pp = 0; pp < k - 1; pp++)
             for (int q = pp + 1; q < k; q++) {
-                double apq = A[pp * kMaxSpace + q];
+                const double apq = A[pp * kSolveLd + q];
                 if (apq == 0.0) continue;
-                double app = A[pp * kMaxSpace + pp], aqq = A[q * kMaxSpace + q];
-                double tau = (aqq - app) / (2.0 * apq);
-                double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
-                for (int r = 0; r < k; r++) {
-                    double arp = A[r * kMaxSpace + pp], arq = A[r * kMaxSpace + q];
-                    A[r * kMaxSpace + pp] = c * arp - sn * arq;
-                    A[r * kMaxSpace + q] = sn * arp + c * arq;
+                const double app = A[pp * kSolveLd + pp], aqq = A[q * kSolveLd + q];
+                __syncwarp();   // every lane has read the rotation's entries
+                if (fabs(apq) <= 1e-18 * (fabs(app) + fabs(aqq))) {
+                    if (lane == 0) A[pp * kSolveLd + q] = A[q * kSolveLd + pp] = 0.0;
+                    __syncwarp();
+                    continue;
                 }
-                for (int r = 0; r < k; r++) {
-                    double apr = A[pp * kMaxSpace + r], aqr = A[q * kMaxSpace + r];
-                    A[pp * kMaxSpace + r] = c * apr - sn * aqr;
-                    A[q * kMaxSpace + r] = sn * apr + c * aqr;
+                const double tau = (aqq - app) / (2.0 * apq);
+                const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+                if (lane < k) {
+                    const double arp = A[lane * kSolveLd + pp], arq = A[lane * kSolveLd + q];
+                    A[lane * kSolveLd + pp] = c * arp - sn * arq;
+                    A[lane * kSolveLd + q] = sn * arp + c * arq;
                 }
-                for (int r = 0; r < k; r++) {
-                    double vrp = V[r * kMaxSpace + pp], vrq = V[r * kMaxSpace + q];
-                    V[r * kMaxSpace + pp] = c * vrp - sn * vrq;
-                    V[r * kMaxSpace + q] = sn * vrp + c * vrq;
+                __syncwarp();
+                if (lane < k) {
+                    const double apr = A[pp * kSolveLd + lane], aqr = A[q * kSolveLd + lane];
+                    A[pp * kSolveLd + lane] = c * apr - sn * aqr;
+                    A[q * kSolveLd + lane] = sn * apr + c * aqr;
+                    const double vrp = V[lane * kSolveLd + pp], vrq = V[lane * kSolveLd + q];
+                    V[lane * kSolveLd + pp] = c * vrp - sn * vrq;
+                    V[lane * kSolveLd + q] = sn * vrp + c * vrq;
                 }
+                __syncwarp();
             }
-    }
-    // the nk lowest eigenpairs in ascending order; each vector's largest
-    // component made positive (deterministic sign)
-    bool used[kMaxSpace];
-    for (int i = 0; i < k; i++) used[i] = false;
-    for (int r = 0; r < nk; r++) {
-        int best = -1;
-        for (int i = 0; i < k; i++)
-            if (!used[i] && (best < 0 || A[i * kMaxSpace + i] < A[best * kMaxSpace + best])) best = i;
-        used[best] = true;
-        theta[r] = A[best * kMaxSpace + best];
-        int big = 0;
-        for (int i = 1; i < k; i++)
-            if (fabs(V[i * kMaxSpace + best]) > fabs(V[big * kMaxSpace + best])) big = i;
-        double sg = V[big * kMaxSpace + best] < 0 ? -1.0 : 1.0;
-        for (int i = 0; i < k; i++) y[r * kMaxSpace + i] = sg * V[i * kMaxSpace + best];
     }
 }
 
-// One block per problem: finish the subspace column and solve the projected problem.
-__device__ __forceinline__ void solve_kernel_body(const DavProb *__restrict__ probs, DavState *__restrict__ st,
-                             const double *__restrict__ part, double *__restrict__ gs, double *__restrict__ ys, int w_) {
-    const int i = w_;
+// One warp per problem: finish the subspace column and solve the projected
+// problem (its kKeep lowest Ritz pairs).
+__device__ __forceinline__ void solve_warp_body(const DavProb *__restrict__ probs, DavState *__restrict__ st,
+                                                const double *__restrict__ part, double *__restrict__ gs,
+                                                double *__restrict__ ys, int i, double *A, double *V) {
+    const int lane = threadIdx.x & 31;
     DavState s = st[i];
     if (!s.active) return;
-    const DavProb p = probs[i];
+    const DavProb &p = probs[i];
     const int k = s.newest + 1;
     double *Gm = gs + (long long)i * kMaxSpace * kMaxSpace;
-    __shared__ double col[kMaxSpace + 1];
-    if (threadIdx.x < k) {
+    if (lane < k) {
         double v = 0.0;
-        for (int w = 0; w < p.nitem; w++) v += part[(long long)(p.item0 + w) * kNP + threadIdx.x];
-        col[threadIdx.x] = v;
+        for (int w = 0; w < p.nitem; w++) v += part[(long long)(p.item0 + w) * kNP + lane];
+        Gm[lane * kMaxSpace + s.newest] = v;
+        Gm[s.newest * kMaxSpace + lane] = v;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int j = 0; j < k; j++) {
-            Gm[j * kMaxSpace + s.newest] = col[j];
-            Gm[s.newest * kMaxSpace + j] = col[j];
-        }
-        double A[kMaxSpace * kMaxSpace], V[kMaxSpace * kMaxSpace], y[kKeep * kMaxSpace], th[kKeep];
-        for (int a = 0; a < k; a++)
-            for (int b = 0; b < k; b++) A[a * kMaxSpace + b] = 0.5 * (Gm[a * kMaxSpace + b] + Gm[b * kMaxSpace + a]);
+    __syncwarp();
+    if (lane < k)
+        for (int b = 0; b < k; b++) A[lane * kSolveLd + b] = 0.5 * (Gm[lane * kMaxSpace + b] + Gm[b * kMaxSpace + lane]);
+    __syncwarp();
+    jacobi_warp(A, V, k, lane);
+    if (lane == 0) {
+        // the nk lowest eigenpairs in ascending order; each vector's largest
+        // component made positive (deterministic sign)
         const int nk = k < kKeep ? k : kKeep;
-        jacobi_lowest(A, V, k, nk, th, y);
         double *yo = ys + (long long)i * kYStride;
+        bool used[kMaxSpace];
+        for (int j = 0; j < k; j++) used[j] = false;
         for (int r = 0; r < kKeep; r++) {
-            for (int j = 0; j < kNP; j++) yo[r * kNP + j] = (r < nk && j < k) ? y[r * kMaxSpace + j] : 0.0;
-            yo[r * kNP + kMaxSpace] = r < nk ? th[r] : 0.0;
+            if (r >= nk) {
+                for (int j = 0; j < kNP; j++) yo[r * kNP + j] = 0.0;
+                continue;
+            }
+            int best = -1;
+            for (int j = 0; j < k; j++)
+                if (!used[j] && (best < 0 || A[j * kSolveLd + j] < A[best * kSolveLd + best])) best = j;
+            used[best] = true;
+            int big = 0;
+            for (int j = 1; j < k; j++)
+                if (fabs(V[j * kSolveLd + best]) > fabs(V[big * kSolveLd + best])) big = j;
+            const double sg = V[big * kSolveLd + best] < 0 ? -1.0 : 1.0;
+            for (int j = 0; j < kNP; j++) yo[r * kNP + j] = j < k ? sg * V[j * kSolveLd + best] : 0.0;
+            yo[r * kNP + kMaxSpace] = A[best * kSolveLd + best];
+            if (r == 0) s.theta = A[best * kSolveLd + best];
         }
-        s.theta = th[0];
         s.iters += 1;
         st[i] = s;
     }
+    __syncwarp();   // A and V are reused by the warp's next problem
 }
 
-__global__ void solve_kernel(const DavProb *__restrict__ probs, DavState *__restrict__ st,
-                             const double *__restrict__ part, double *__restrict__ gs, double *__restrict__ ys, int nprob_) {
-    for (int w = blockIdx.x; w < nprob_; w += gridDim.x) {
-        solve_kernel_body(probs, st, part, gs, ys, w);
-        __syncthreads();   // shared memory is reused by the next body
-    }
+__global__ void __launch_bounds__(32 * kSolveWarps) solve_kernel(const DavProb *__restrict__ probs,
+                                                                 DavState *__restrict__ st,
+                                                                 const double *__restrict__ part,
+                                                                 double *__restrict__ gs, double *__restrict__ ys,
+                                                                 int nprob_) {
+    __shared__ double sm[kSolveWarps][2][kMaxSpace * kSolveLd];
+    const int warp = threadIdx.x >> 5;
+    for (int w = blockIdx.x * kSolveWarps + warp; w < nprob_; w += gridDim.x * kSolveWarps)
+        solve_warp_body(probs, st, part, gs, ys, w, sm[warp][0], sm[warp][1]);
 }
 
 // For the targeted Ritz pair (theta, y): t = sum_j y_j (S_j - theta B_j);
@@ -805,6 +824,28 @@ __global__ void __launch_bounds__(256) ritz_out_kernel(const DavProb *__restrict
     for (int w = blockIdx.x; w < nitem_; w += gridDim.x) ritz_out_kernel_body(probs, st, items, ys, w);
 }
 
+// Selected-CI problems: sigma of the newest slot zeroed outside the selection
+// (the iteration then stays in the span of the selected determinants).
+__device__ __forceinline__ void mask_sigma_kernel_body(const DavProb *__restrict__ probs,
+                                                         const DavState *__restrict__ st,
+                                                         const WorkItem *__restrict__ items, int w_) {
+    const WorkItem it = items[w_];
+    const DavProb &p = probs[it.prob];
+    if (!p.mask) return;
+    const DavState s = st[it.prob];
+    if (!s.active) return;
+    double *S = p.S + (long long)s.newest * p.ndet;
+    const long long end = min(it.start + (long long)kVecChunk, p.ndet);
+    for (long long I = it.start + threadIdx.x; I < end; I += blockDim.x)
+        if (!p.mask[I]) S[I] = 0.0;
+}
+
+__global__ void __launch_bounds__(256) mask_sigma_kernel(const DavProb *__restrict__ probs,
+                                                         const DavState *__restrict__ st,
+                                                         const WorkItem *__restrict__ items, int nitem_) {
+    for (int w = blockIdx.x; w < nitem_; w += gridDim.x) mask_sigma_kernel_body(probs, st, items, w);
+}
+
 // ------------------------------------------------------------------ driver
 
 int dav_init(ifci_handle_t h, DavBatch &b, const HdiagDesc *d_hd, cudaStream_t s) {
@@ -845,10 +886,16 @@ static int dav_step(ifci_handle_t h, DavBatch &b, SigmaPlan &hi_plan, SigmaPlan 
         IFCI_TRY(run_sigma(h, *lo_plan, b.precision, D, G, s));
         IFCI_TRY(sector_move(false, d_lo));
     }
+    if (b.any_mask) {
+        ProfScope ps(h, s, PK_OTHER);
+        mask_sigma_kernel<<<gi, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, nitem);
+        IFCI_LAUNCH_CHECK(h);
+    }
     ProfScope vec_scope(h, s, PK_VECTOR);
     dots_kernel<<<gi, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part, nitem);
     IFCI_LAUNCH_CHECK(h);
-    solve_kernel<<<gp, 32, 0, s>>>(b.d_probs, b.d_state, b.d_part, b.d_gs, b.d_y, b.nprob);
+    solve_kernel<<<stride_grid(h->device, (b.nprob + kSolveWarps - 1) / kSolveWarps, 8), 32 * kSolveWarps, 0, s>>>(
+        b.d_probs, b.d_state, b.d_part, b.d_gs, b.d_y, b.nprob);
     IFCI_LAUNCH_CHECK(h);
     residual_kernel<<<gi, 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_y, b.max_space, b.d_part, nitem);
     IFCI_LAUNCH_CHECK(h);

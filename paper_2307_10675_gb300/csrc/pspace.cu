@@ -20,6 +20,7 @@
 // the two single signs.
 #include "dav_driver.cuh"
 #include "hamiltonian.cuh"
+#include "slater.cuh"
 
 namespace ifci {
 
@@ -29,83 +30,6 @@ constexpr int kPsp = kPspMax;   // pair functions in the guess space
 constexpr int kSelThreads = 256;
 constexpr int kSelPer = 4;      // candidates kept per thread during selection
 constexpr int kSelCand = kSelThreads * kSelPer;
-
-__device__ __forceinline__ int between_parity(uint32_t m, int p, int q) {
-    const int lo = min(p, q), hi = max(p, q);
-    const uint32_t mask = ((1u << hi) - 1u) & ~((2u << lo) - 1u);
-    return __popc(m & mask) & 1;
-}
-
-__device__ __forceinline__ double eri4(const double *eri, int np, int p, int q, int r, int s) {
-    return eri[(long long)pair_of(p, q) * np + pair_of(r, s)];
-}
-
-// <ia ib | H | ja jb> for alpha/beta occupation masks of n orbitals.
-__device__ double h_element(int n, const double *__restrict__ h1, const double *__restrict__ eri, uint32_t ia,
-                            uint32_t ib, uint32_t ja, uint32_t jb) {
-    const int np = n * (n + 1) / 2;
-    const uint32_t da = ia ^ ja, db = ib ^ jb;
-    const int na = __popc(da) / 2, nb = __popc(db) / 2;
-    if (na + nb > 2) return 0.0;
-    if (na + nb == 0) {
-        double e = 0.0, two = 0.0;
-        for (uint32_t x = ia; x; x &= x - 1) e += h1[(__ffs(x) - 1) * (n + 1)];
-        for (uint32_t x = ib; x; x &= x - 1) e += h1[(__ffs(x) - 1) * (n + 1)];
-        for (uint32_t x = ia; x; x &= x - 1) {
-            const int p = __ffs(x) - 1;
-            for (uint32_t y = ia; y; y &= y - 1) {
-                const int q = __ffs(y) - 1;
-                two += eri4(eri, np, p, p, q, q) - eri4(eri, np, p, q, q, p);
-            }
-            for (uint32_t y = ib; y; y &= y - 1) two += 2.0 * eri4(eri, np, p, p, __ffs(y) - 1, __ffs(y) - 1);
-        }
-        for (uint32_t x = ib; x; x &= x - 1) {
-            const int p = __ffs(x) - 1;
-            for (uint32_t y = ib; y; y &= y - 1) {
-                const int q = __ffs(y) - 1;
-                two += eri4(eri, np, p, p, q, q) - eri4(eri, np, p, q, q, p);
-            }
-        }
-        return e + 0.5 * two;
-    }
-    if (na + nb == 1) {
-        // one electron j -> a of spin s; "same" = the other electrons of spin s, "other" = the other spin
-        const bool alpha = na == 1;
-        const uint32_t bra = alpha ? ia : ib, ket = alpha ? ja : jb, other = alpha ? ib : ia;
-        const int a = __ffs(bra & ~ket) - 1, j = __ffs(ket & ~bra) - 1;
-        double v = h1[a * n + j];
-        for (uint32_t x = bra & ket; x; x &= x - 1) {
-            const int k = __ffs(x) - 1;
-            v += eri4(eri, np, a, j, k, k) - eri4(eri, np, a, k, k, j);
-        }
-        for (uint32_t x = other; x; x &= x - 1) {
-            const int k = __ffs(x) - 1;
-            v += eri4(eri, np, a, j, k, k);
-        }
-        return between_parity(ket, a, j) ? -v : v;
-    }
-    if (na == 1 && nb == 1) {
-        const int a = __ffs(ia & ~ja) - 1, j = __ffs(ja & ~ia) - 1;
-        const int b = __ffs(ib & ~jb) - 1, l = __ffs(jb & ~ib) - 1;
-        const double v = eri4(eri, np, a, j, b, l);
-        return (between_parity(ja, a, j) ^ between_parity(jb, b, l)) ? -v : v;
-    }
-    // two electrons of one spin: j1 -> a1, then j2 -> a2
-    const bool alpha = na == 2;
-    const uint32_t bra = alpha ? ia : ib, ket = alpha ? ja : jb;
-    uint32_t up = bra & ~ket, dn = ket & ~bra;
-    const int a1 = __ffs(up) - 1;
-    up &= up - 1;
-    const int a2 = __ffs(up) - 1;
-    const int j1 = __ffs(dn) - 1;
-    dn &= dn - 1;
-    const int j2 = __ffs(dn) - 1;
-    const int s1 = between_parity(ket, a1, j1);
-    const uint32_t mid = ket ^ (1u << j1) ^ (1u << a1);
-    const int s2 = between_parity(mid, a2, j2);
-    const double v = eri4(eri, np, a1, j1, a2, j2) - eri4(eri, np, a1, j2, a2, j1);
-    return (s1 ^ s2) ? -v : v;
-}
 
 // Per problem: the kPsp lowest-diagonal canonical determinants (I_a <= I_b).
 // Each thread keeps its kSelPer lowest over a strided scan, then the block
@@ -190,7 +114,7 @@ __device__ __forceinline__ void psp_solve_kernel_body(const DavProb *__restrict_
     extern __shared__ double psm[];
     double *A = psm;                       // [kPsp][kPsp]
     double *V = psm + kPsp * kPsp;         // [kPsp][kPsp]
-    __shared__ double red[kPsp];
+    __shared__ double red[kPsp], red2[kPsp];
     const DavProb p = probs[w_];
     const HdiagDesc d = hdd[w_];
     const int P = pcount[w_];
@@ -250,17 +174,27 @@ __device__ __forceinline__ void psp_solve_kernel_body(const DavProb *__restrict_
         }
     }
     __syncthreads();
+    // sweeps until the off-diagonal part is below 1e-26 of |A|_F^2 (a start
+    // guess needs no more); a rotation whose A_pq is below 1e-18 (|A_pp| +
+    // |A_qq|) only sets A_pq = A_qp = 0
     for (int sweep = 0; sweep < 40; sweep++) {
-        double off = 0.0;
+        double off = 0.0, all = 0.0;
         if (t < P)
-            for (int c = 0; c < P; c++)
-                if (c != t) off += A[t * kPsp + c] * A[t * kPsp + c];
+            for (int c = 0; c < P; c++) {
+                const double a2 = A[t * kPsp + c] * A[t * kPsp + c];
+                all += a2;
+                if (c != t) off += a2;
+            }
         red[t] = off;
+        red2[t] = all;
         __syncthreads();
-        double tot = 0.0;
-        for (int i = 0; i < P; i++) tot += red[i];
+        double tot = 0.0, fro = 0.0;
+        for (int i = 0; i < P; i++) {
+            tot += red[i];
+            fro += red2[i];
+        }
         __syncthreads();
-        if (tot < 1e-26) break;
+        if (tot <= 1e-26 * fro || tot == 0.0) break;
         for (int pp = 0; pp < P - 1; pp++)
             for (int q = pp + 1; q < P; q++) {
                 // every thread reads the same settled entries and derives the same
@@ -268,7 +202,14 @@ __device__ __forceinline__ void psp_solve_kernel_body(const DavProb *__restrict_
                 // functions beyond a double excitation apart) are skipped
                 const double apq = A[pp * kPsp + q];
                 if (fabs(apq) < 1e-300) continue;
-                const double tau = (A[q * kPsp + q] - A[pp * kPsp + pp]) / (2.0 * apq);
+                const double app = A[pp * kPsp + pp], aqq = A[q * kPsp + q];
+                if (fabs(apq) <= 1e-18 * (fabs(app) + fabs(aqq))) {
+                    __syncthreads();   // every thread has read A[pp][q]
+                    if (t == 0) A[pp * kPsp + q] = A[q * kPsp + pp] = 0.0;
+                    __syncthreads();
+                    continue;
+                }
+                const double tau = (aqq - app) / (2.0 * apq);
                 const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                 const double c = 1.0 / sqrt(1.0 + tt * tt), sn = tt * c;
                 __syncthreads();   // every thread has read A[pp][q], A[pp][pp], A[q][q]
