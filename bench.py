@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c4", choices=["c4", "c1"],
                     help="c4: 40-body chain (10,700 CI problems); c1: 24-body chain (2324)")
-    ap.add_argument("--precision", default="fp64e", choices=["fp64", "fp32", "bf16", "fp64e"])
+    ap.add_argument("--precision", default="fp64e", choices=["fp64", "fp32", "tf32", "bf16", "fp64e"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 and mixed comparison on the sample")
     ap.add_argument("--compare-fraction", type=float, default=0.05,
                     help="seeded fraction of the 3-body sets in the path comparison (all 1- and 2-body sets)")
@@ -62,16 +62,18 @@ def parse():
     ap.add_argument("--sample-seconds", type=float, default=20.0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (max_space, det_budget, graph_iters) and use the library defaults")
-    ap.add_argument("--autotune-fraction", type=float, default=0.05,
+    ap.add_argument("--autotune-fraction", type=float, default=0.25,
                     help="seeded fraction of the largest body sets in the autotuner's sample")
     ap.add_argument("--dump", default="", help="--case c4: directory for per-set energies")
     ap.add_argument("--det-budget", type=int, default=0,
                     help="determinants per sigma wave (0: library default)")
-    ap.add_argument("--case", default="increments", choices=["increments", "sigma", "c2", "c4"],
+    ap.add_argument("--case", default="increments", choices=["increments", "sigma", "c2", "c4", "hbci", "fourbody"],
                     help="sigma: time ifci_sigma alone on the workload's largest problem, CAS(6e,18o) "
                          "(the small case for kernel profiles); c2: one CAS(14e,14o) CI per precision; "
                          "c4: 3-body iFCI of the 40-body chain in every precision on all 10,700 sets "
-                         "(totals and per-set differences), plus the RDM backward")
+                         "(totals and per-set differences), plus the RDM backward; hbci: the workload's "
+                         "expansion with HBCI increments at the paper's thresholds against exact CI; "
+                         "fourbody: sigma and Davidson of CAS(8e,24o), the largest 4-body space")
     return ap.parse_args()
 
 
@@ -233,13 +235,18 @@ def oracle_conn(n, m):
     return 1 + 2 * (s1 + s2) + s1 * s1
 
 
-def oracle_baseline(chain, max_order, seconds, seed=11):
+def oracle_baseline(chain, max_order, seconds, seed=11, check_large=True, prior_check=None):
     """Times the oracle on a seeded sample of the workload's body sets for about
     ``seconds`` and extrapolates the whole workload's time.  Two regimes, as
     the oracle solves them: dense eigh (ndet <= oracle DENSE_MAX), every such
     set timed or its mean taken; Lanczos (matrix-free Slater–Condon matvecs),
     calibrated on the sampled sets up to 30,000 determinants with the model
-    t = a * ndet * (determinants connected per row)."""
+    t = a * ndet * (determinants connected per row).  ``check_large``: one
+    matvec of the workload's largest space and one of the largest sampled
+    set are timed as well; the ratio of their cost per ndet * connection
+    rescales the model for the sets above the calibration range (their
+    Lanczos iteration count is taken equal to the sampled sets' mean);
+    ``prior_check`` reuses the ratio of an earlier call."""
     from oracle import fci
     subs = subset_sizes(chain, max_order)
     rng = np.random.default_rng(seed)
@@ -247,7 +254,7 @@ def oracle_baseline(chain, max_order, seconds, seed=11):
     fci.lib()                       # build/load before timing
     dense = [i for i in order if math.comb(subs[i][1], subs[i][2]) ** 2 <= fci.DENSE_MAX]
     lanc = [i for i in order if fci.DENSE_MAX < math.comb(subs[i][1], subs[i][2]) ** 2 <= 30000]
-    t_dense, n_dense, t_lanc, m_lanc, n_lanc = 0.0, 0, 0.0, 0.0, 0
+    t_dense, n_dense, t_lanc, m_lanc, n_lanc, it_lanc = 0.0, 0, 0.0, 0.0, 0, 0
     for i in dense:
         X, n, k = subs[i]
         t0 = time.perf_counter()
@@ -256,24 +263,54 @@ def oracle_baseline(chain, max_order, seconds, seed=11):
         n_dense += 1
         if t_dense > 0.25 * seconds:
             break
+    biggest = None
     for i in lanc:
         X, n, k = subs[i]
         t0 = time.perf_counter()
-        fci.solve_subsystem(chain, X)
+        r = fci.solve_subsystem(chain, X)
         t_lanc += time.perf_counter() - t0
         m_lanc += math.comb(n, k) ** 2 * oracle_conn(n, k)
         n_lanc += 1
+        it_lanc += r.iterations
+        if biggest is None or math.comb(n, k) > math.comb(biggest[1], biggest[2]):
+            biggest = subs[i]
         if t_lanc > 0.75 * seconds:
             break
+    unit = t_lanc / max(m_lanc, 1.0)
+    scale_large, check = 1.0, None
+    large = max(subs, key=lambda t: math.comb(t[1], t[2]))
+    if prior_check:
+        scale_large, check = prior_check["matvec_unit_cost_ratio"], prior_check
+    elif check_large and biggest is not None and math.comb(large[1], large[2]) ** 2 > 30000:
+        def matvec_unit(t):
+            X, n, k = t
+            H = fci.Hamiltonian(fci.subsystem(chain, X))
+            x = np.random.default_rng(3).normal(size=H.ndet)
+            t0 = time.perf_counter()
+            H.matvec(x)
+            return (time.perf_counter() - t0) / (H.ndet * oracle_conn(n, k))
+        u_small, u_large = matvec_unit(biggest), matvec_unit(large)
+        scale_large = u_large / u_small
+        check = {"matvec_unit_cost_ratio": scale_large, "large_set": list(large[0]),
+                 "large_ndet": math.comb(large[1], large[2]) ** 2, "calibration_set": list(biggest[0]),
+                 "calibration_ndet": math.comb(biggest[1], biggest[2]) ** 2,
+                 "sampled_lanczos_iterations_mean": it_lanc / max(n_lanc, 1),
+                 "predicted_seconds_largest_set": unit * scale_large * math.comb(large[1], large[2]) ** 2 *
+                                                  oracle_conn(large[1], large[2])}
     nd_dense = sum(1 for _, n, k in subs if math.comb(n, k) ** 2 <= fci.DENSE_MAX)
-    model_rest = sum(math.comb(n, k) ** 2 * oracle_conn(n, k) for _, n, k in subs
-                     if math.comb(n, k) ** 2 > fci.DENSE_MAX)
-    t_total = t_dense / max(n_dense, 1) * nd_dense + t_lanc / max(m_lanc, 1.0) * model_rest
-    return {"value": len(subs) / t_total, "unit": UNIT, "cores": fci.num_threads(), "kind": "oracle",
-            "sample": (f"{n_dense} dense and {n_lanc} Lanczos body sets (<= 30,000 determinants) of the workload, "
-                       f"seeded, timed in {t_dense + t_lanc:.1f} s; whole-workload time extrapolated per regime "
-                       f"(dense: mean per set; Lanczos: ndet x connected determinants per row), "
-                       f"{t_total:.0f} s for {len(subs)} sets")}
+    model_mid = sum(math.comb(n, k) ** 2 * oracle_conn(n, k) for _, n, k in subs
+                    if fci.DENSE_MAX < math.comb(n, k) ** 2 <= 30000)
+    model_big = sum(math.comb(n, k) ** 2 * oracle_conn(n, k) for _, n, k in subs if math.comb(n, k) ** 2 > 30000)
+    t_total = t_dense / max(n_dense, 1) * nd_dense + unit * (model_mid + scale_large * model_big)
+    out = {"value": len(subs) / t_total, "unit": UNIT, "cores": fci.num_threads(), "kind": "oracle",
+           "sample": (f"{n_dense} dense and {n_lanc} Lanczos body sets (<= 30,000 determinants) of the workload, "
+                      f"seeded, timed in {t_dense + t_lanc:.1f} s; whole-workload time extrapolated per regime "
+                      f"(dense: mean per set; Lanczos: ndet x connected determinants per row, the cost per unit "
+                      f"above 30,000 determinants rescaled by a timed matvec of the largest space), "
+                      f"{t_total:.0f} s for {len(subs)} sets")}
+    if check:
+        out["model_check"] = check
+    return out
 
 
 # ---------------------------------------------------------------- main
@@ -290,12 +327,15 @@ def main():
         steps = args.steps if args.steps is not None else 1
         chain = workload(0, args.workload)
         per = max(3.0, args.sample_seconds / 2)
+        prior = None
         for _ in range(args.warmup):
-            oracle_baseline(chain, args.max_order, per)
+            w = oracle_baseline(chain, args.max_order, per, prior_check=prior)
+            prior = w.get("model_check")
         vals = []
         t0 = time.perf_counter()
         for _ in range(steps):
-            r = oracle_baseline(chain, args.max_order, per)
+            r = oracle_baseline(chain, args.max_order, per, prior_check=prior)
+            prior = r.get("model_check")
             vals.append(r["value"])
         el = time.perf_counter() - t0
         v = float(np.mean(vals))
@@ -305,7 +345,7 @@ def main():
                 "config": {"workload": WORKLOAD_NAMES[args.workload], "seed": chain.seed,
                            "sample": "bounded oracle sample per step"},
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-                                 "sample": r["sample"]},
+                                 "sample": r["sample"], "model_check": r.get("model_check")},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
@@ -319,6 +359,10 @@ def main():
         return c2_case(args, torch, ifci)
     if args.case == "c4":
         return c4_case(args, torch, ifci)
+    if args.case == "hbci":
+        return hbci_case(args, torch, ifci)
+    if args.case == "fourbody":
+        return fourbody_case(args, torch, ifci)
 
     dist = None
     if world > 1:
@@ -385,7 +429,7 @@ def main():
     handle.profile_enable(False)
 
     # sigma FLOPs of a step: sigma builds per problem x 2 ndet npair^2 (the
-    # SURVEY's algorithmic count), and the same over the pairs the FP64E
+    # algorithmic count of the Knowles–Handy contraction), and the same over the pairs the FP64E
     # contraction runs over (a set whose bodies split into decoupled groups
     # contracts only the pairs within each group: its H' has no others)
     its = outp["iters"]
@@ -686,6 +730,92 @@ def c4_case(args, torch, ifci):
         res[name]["speedup_vs_fp64"] = res[name]["increments_per_s"] / res["fp64"]["increments_per_s"]
     print(json.dumps({"case": "c4", "workload": WORKLOAD_NAMES["c4"], "davidson": {"r_tol": R_TOL, "e_tol": E_TOL},
                       "runs": res}), flush=True)
+    return 0
+
+
+def hbci_case(args, torch, ifci):
+    """The workload's expansion (default 40-body chain to 3 bodies) with every
+    E_X from HBCI at the paper's thresholds (eps1 = 1 mHa, eps2 = 1 µHa) and
+    with exact CI (FP64E), each timed once after one untimed run; prints
+    increments/s of both, the totals and the largest per-set difference."""
+    dev = torch.device("cuda", 0)
+    chain = workload(0, args.workload)
+    res = {}
+    with ifci.Handle(0, 0) as h:
+        sysd = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=dev),
+                                 torch.tensor(chain.eri_packed(), device=dev))
+        for name, extra in (("fci", {}), ("hbci", {"hbci_max_rounds": 50, "hbci_eps1": 1e-3, "hbci_eps2": 1e-6})):
+            opts = ifci.davidson_opts("fp64e", r_tol=R_TOL, e_tol=E_TOL, max_iter=300, **extra)
+            ifci.ifci_increments(h, sysd, args.max_order, opts)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            out = ifci.ifci_increments(h, sysd, args.max_order, opts)
+            torch.cuda.synchronize(dev)
+            res[name] = (time.perf_counter() - t0, out)
+    nsub = len(res["fci"][1]["eps"])
+    d = res["hbci"][1]["e_x"] - res["fci"][1]["e_x"]
+    line = {"case": "hbci", "workload": WORKLOAD_NAMES[args.workload], "eps1": 1e-3, "eps2": 1e-6,
+            "fci": {"seconds": res["fci"][0], "increments_per_s": nsub / res["fci"][0],
+                    "e_total": res["fci"][1]["e_total"]},
+            "hbci": {"seconds": res["hbci"][0], "increments_per_s": nsub / res["hbci"][0],
+                     "e_total": res["hbci"][1]["e_total"],
+                     "mean_variational_steps": float(np.mean(res["hbci"][1]["iters"]))},
+            "e_total_hbci_minus_fci": res["hbci"][1]["e_total"] - res["fci"][1]["e_total"],
+            "max_abs_e_x_difference": float(np.max(np.abs(d))),
+            "largest_e_x_differences": [[list(ifci.body_subsets(chain.nbody, args.max_order)[i]), float(d[i])]
+                                        for i in np.argsort(-np.abs(d))[:5]],
+            "min_e_x_difference": float(np.min(d)),
+            "note": "HBCI's variational step runs the FCI sigma over the whole space (selection kept by a mask): "
+                    "it reproduces the paper's approximation, not its savings"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def fourbody_case(args, torch, ifci):
+    """CAS(8e,24o) of the 24-body chain (four 6-orbital bodies; 10,626 strings,
+    112,911,876 determinants, 300 pairs): the FP64E sigma (K chunks and row
+    slabs of G) timed over a few calls, then one Davidson solve of the space."""
+    from synth import chain_24_uneven, random_ci_vector
+    dev = torch.device("cuda", 0)
+    chain = chain_24_uneven()
+    X = tuple(b for b, sz in enumerate(chain.body_sizes) if sz == 6)[:4]
+    n, m = 24, 4
+    steps = args.steps if args.steps is not None else 3
+    with ifci.Handle(0, 0) as h:
+        sysd = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=dev),
+                                 torch.tensor(chain.eri_packed(), device=dev))
+        h1, eri, ecore = ifci.ifci_frozen_core(h, sysd, X)
+        t = ifci.ifci_build_strings(h, n, m)
+        nstr = math.comb(n, m)
+        c = torch.tensor(random_ci_vector(nstr, nstr, seed=1, symmetric=True), device=dev).reshape(-1)
+        ifci.ifci_sigma(h, t, h1, eri, c, precision=ifci.IFCI_FP64E, spin_symmetric=True)
+        torch.cuda.synchronize(dev)
+        h.profile_enable(True)
+        stream = torch.cuda.current_stream(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            ifci.ifci_sigma(h, t, h1, eri, c, precision=ifci.IFCI_FP64E, spin_symmetric=True)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        prof = h.profile_read()
+        h.profile_enable(False)
+        ms = ev0.elapsed_time(ev1) / steps
+        del c
+        prob = ifci.CIProblem(n, m, h1, eri, ecore)
+        t0 = time.perf_counter()
+        e, it, st = ifci.ifci_davidson_batched(h, [prob], ifci.davidson_opts("fp64e", r_tol=R_TOL, e_tol=E_TOL,
+                                                                             max_iter=300))
+        torch.cuda.synchronize(dev)
+        dav_s = time.perf_counter() - t0
+    nd, fl = cost_of(n, m)
+    c_ms = prof["contract_hi"][0] / steps
+    line = {"case": "fourbody", "workload": "CAS(8e,24o) of chain-24-uneven (bodies %s), %d determinants" % (X, nd),
+            "sigma_ms": ms, "sigma_algorithmic_tflops": fl / (ms / 1000.0) / 1e12,
+            "contract_hi_ms": c_ms, "contract_hi_tflops_algorithmic": fl / (c_ms / 1000.0) / 1e12,
+            "kernel_ms_per_sigma": {k: v[0] / steps for k, v in prof.items()},
+            "davidson": {"seconds": dav_s, "energy": float(e[0]), "sigma_builds": int(it[0]), "status": int(st[0])}}
+    print(json.dumps(line), flush=True)
     return 0
 
 

@@ -59,7 +59,8 @@ typedef enum {
 typedef enum {
     IFCI_FP64 = 0, /* every step in FP64 */
     IFCI_FP32 = 1, /* sigma contraction with FP32 inputs, FP32 accumulation */
-    IFCI_TF32 = 2, /* sigma contraction on tensor cores, TF32 inputs, FP32 accumulation */
+    IFCI_TF32 = 2, /* sigma contraction on tensor cores, TF32 inputs (rounded with
+                      cvt.rna, to nearest, ties away from zero), FP32 accumulation */
     IFCI_BF16 = 3, /* sigma contraction on tensor cores, BF16 inputs, FP32 accumulation */
     IFCI_FP64E = 4 /* sigma contraction to ~FP64 accuracy on FP16 tensor cores: both
                       operands split into 5 slices of 8-bit integers, the 15 leading
@@ -69,7 +70,7 @@ typedef enum {
 
 /* Flag OR-ed into ifci_sigma's precision: the caller asserts that c is
  * spin-flip symmetric, c[Ia][Ib] = c[Ib][Ia] (the singlet sector the Davidson
- * solver works in).  The tensor-core precisions (BF16, FP64E) then gather the
+ * solver works in).  The tensor-core precisions (BF16, TF32, FP64E) then gather the
  * alpha excitations only and return S + S^T, S the sigma of the alpha-only
  * intermediate, which equals H c for such c (a restatement of the sigma
  * build, not a step of the paper).  Ignored by FP64 and FP32, and by
@@ -147,6 +148,14 @@ typedef struct {
  *   sigma : device double[nstr*nstr], output (must not alias c).
  *   precision : ifci_precision_t of the contraction (FP64 exact path;
  *               the others round the contraction inputs, FP32 accumulate).
+ * Sizes: BF16 and TF32 take npair <= 256 (norb <= 22), FP64E npair <= 304
+ * (norb <= 24; above 204 pairs in K chunks of 192 whose exact int64 partial
+ * sums are added), else UNSUPPORTED.  The intermediates take
+ * 2 * npair * nstr^2 elements of the precision's storage type; a
+ * spin-symmetric FP64E call above 2^31 G elements runs in row slabs of at
+ * most 2^31 (16 GB), the scatter adding each slab's contribution into an
+ * int64 accumulator, with the same result bit for bit.  Workspace beyond the
+ * device's memory fails with OOM.
  * Asynchronous on `stream`; uses handle workspace (grows it if needed). */
 int ifci_sigma(ifci_handle_t handle, const ifci_strings_t *str,
                const double *h1, const double *eri, const double *c, double *sigma,
@@ -245,7 +254,10 @@ typedef struct {
                             precision always finishes on exact sigmas. */
     int hi_precision;    /* mixed mode: sigma of restart vectors, IFCI_FP64 or IFCI_FP64E
                             (default IFCI_FP64E) */
-    long long det_budget;/* D elements (npair x determinants) per sigma wave; 0 = 2^31 */
+    long long det_budget;/* D elements (npair x determinants) per sigma wave; 0 = 2^31.
+                            A problem above it alone runs in row slabs of G on the
+                            FP64E path (bit-identical result); on the other paths it
+                            fails with OOM */
     int graph_iters;     /* > 0: Davidson iterations are captured in blocks of this
                             many into one CUDA graph, replayed on a stream of the
                             handle (event-ordered with `stream`); 0 = launched one
@@ -274,6 +286,13 @@ typedef struct {
                             2-5 (which are then taken recursively, screened increments
                             counting as zero), e_x = NaN and status IFCI_SCREENED.
                             0: every set is solved (default 0). */
+    int hbci_max_rounds; /* ifci_increments only.  > 0: every E_X is the HBCI energy
+                            E_var + E_PT2 of ifci_hbci_batched (Methods, HBCI paragraph),
+                            from the reference determinant of X, with at most this many
+                            variational steps; ifci_rdm_backward then returns UNSUPPORTED.
+                            0: exact CI (default 0). */
+    double hbci_eps1;    /* HBCI selection threshold (default 1e-3 Eh, the paper's) */
+    double hbci_eps2;    /* HBCI PT2 screening threshold (default 1e-6 Eh, the paper's) */
 } ifci_davidson_opts_t;
 
 /* Fills opts with the defaults listed above (precision IFCI_FP64). */
@@ -287,9 +306,11 @@ void ifci_davidson_default_opts(ifci_davidson_opts_t *opts);
  * functions (one per decoupled block of that small matrix first) plus a
  * random vector orthogonal to them; thick restarts keep the four lowest Ritz
  * vectors; Ritz roots within 0.3 Eh of the lowest are corrected in turn
- * until resolved.  When H splits into (nearly) decoupled sectors (charge
- * distributions over distant bodies) the lowest sector is found by these
- * heuristics, not by construction.  Mixed precision (precision = BF16/FP32)
+ * until resolved.  When H splits into decoupled sectors (charge
+ * distributions over bodies that no integral above decouple_tol couples),
+ * every sector block is solved as its own problem and the lowest kept
+ * (ifci_davidson_opts_t.decouple_tol), so the lowest eigenvalue over the
+ * sectors is found by construction.  Mixed precision (precision = BF16/TF32/FP32)
  * runs a low-precision phase, then rebuilds exact sigmas (hi_precision) of
  * its kept Ritz vectors and finishes exactly; convergence is only judged on
  * exact sigmas.
@@ -300,6 +321,44 @@ void ifci_davidson_default_opts(ifci_davidson_opts_t *opts);
 int ifci_davidson_batched(ifci_handle_t handle, int nprob, const ifci_problem_t *probs,
                           const ifci_davidson_opts_t *opts, double *energies, int *iters,
                           int *status, ifci_stream_t stream);
+
+/* ---------------------------------------------------------------- HBCI */
+
+typedef struct {
+    double eps1;      /* variational selection threshold (Eh); the paper uses 1e-3 */
+    double eps2;      /* EN-PT2 screening threshold (Eh); the paper uses 1e-6 */
+    int max_rounds;   /* variational steps at most (one Davidson solve each), >= 1 */
+} ifci_hbci_opts_t;
+
+/* ifci_hbci_batched — heat-bath selected CI with an Epstein–Nesbet PT2
+ * correction for each problem (Methods, HBCI paragraph: the solver the paper
+ * runs for every increment).  Per problem:
+ *   1. S = {start_det[i]} (a closed-shell determinant I = Ia * nstr + Ia,
+ *      normally the reference with every bonding orbital doubly occupied);
+ *   2. (E_var, c) = lowest eigenpair of H + e_core on S in the spin-flip-even
+ *      sector (the batched Davidson of ifci_davidson_batched with `dopts`,
+ *      seeded from the previous c, sigma kept on S; decouple_tol ignored);
+ *   3. every determinant a outside S with max_{i in S} |<a|H|i> c_i| > eps1
+ *      joins S with its spin-flip image; back to 2 until none joins or
+ *      max_rounds variational steps were taken;
+ *   4. E_PT2 = sum_{a not in S} (sum_{i in S, |<a|H|i> c_i| > eps2}
+ *      <a|H|i> c_i)^2 / (E_var - <a|H|a> - e_core).
+ * S is a byte mask over the problem's determinant index and the PT2
+ * numerators an FP64 array over it (nstr^2 * 18 bytes of device memory per
+ * problem besides the Davidson's); norb <= 32, nelec_spin <= 7.
+ *   start_det : host int64[nprob].
+ *   e_var, e_pt2 : host double[nprob] (E_HBCI = e_var + e_pt2).
+ *   nsel   : host int64[nprob] or NULL, |S| at the end.
+ *   rounds : host int[nprob] or NULL, variational steps taken.
+ *   status : host int[nprob] or NULL, IFCI_OK or IFCI_ERR_NOT_CONVERGED
+ *            (some Davidson solve of the problem did not converge).
+ *   c_out of a problem (optional): the final c.
+ * Synchronous.  INVALID_ARG for a start determinant that is not closed-shell
+ * or negative thresholds; UNSUPPORTED beyond the sizes above. */
+int ifci_hbci_batched(ifci_handle_t handle, int nprob, const ifci_problem_t *probs,
+                      const long long *start_det, const ifci_davidson_opts_t *dopts,
+                      const ifci_hbci_opts_t *hopts, double *e_var, double *e_pt2,
+                      long long *nsel, int *rounds, int *status, ifci_stream_t stream);
 
 /* ---------------------------------------------------------------- increments */
 
@@ -312,7 +371,7 @@ int ifci_num_subsets(int nbody, int max_order, long long *count);
  *   e_x     : host double[nsub] or NULL, E_X per body set (NaN if screened).
  *   eps     : host double[nsub], increments eps_X.
  *   e_total : host double*, E_0 + sum eps_X.
- *   iters   : host int[nsub] or NULL, sigma builds per set.
+ *   iters   : host int[nsub] or NULL, sigma builds per set (HBCI: variational steps).
  *   status  : host int[nsub] or NULL, per-set Davidson status (IFCI_SCREENED for a
  *             set left out by opts->cnb_threshold).
  * Keeps the converged vectors in the handle when opts->refine >= 0 so that

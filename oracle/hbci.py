@@ -48,6 +48,8 @@ class HBCIResult:
     rounds: int              # variational steps taken
     selected: np.ndarray     # bool[ndet], S
     vector: np.ndarray       # float64[ndet], c (zero outside S)
+    margin1: float = np.inf  # smallest | max_i |H_ai c_i| - eps1 | met in a selection (how
+                             # far every decision was from the threshold)
 
 
 def _flip_even_basis(idx: np.ndarray, flip: np.ndarray) -> np.ndarray:
@@ -77,6 +79,7 @@ def hbci_dense(H: np.ndarray, flip: np.ndarray, start: int, eps1: float, eps2: f
     sel[start] = sel[flip[start]] = True
     diag = np.diag(H)
     rounds = 0
+    margin1 = np.inf
     while True:
         rounds += 1
         idx = np.flatnonzero(sel)
@@ -89,7 +92,10 @@ def hbci_dense(H: np.ndarray, flip: np.ndarray, start: int, eps1: float, eps2: f
             break
         # heat-bath criterion: the largest single contribution |H_ai c_i| over i in S
         contrib = np.abs(H[:, sel] * c[sel][None, :])
-        new = (contrib.max(axis=1) > eps1) & ~sel
+        best = contrib.max(axis=1)
+        if (~sel).any():
+            margin1 = min(margin1, float(np.min(np.abs(best[~sel] - eps1))))
+        new = (best > eps1) & ~sel
         if not new.any():
             break
         new_idx = np.flatnonzero(new)
@@ -99,7 +105,7 @@ def hbci_dense(H: np.ndarray, flip: np.ndarray, start: int, eps1: float, eps2: f
     terms = H[np.ix_(out, sel)] * c[sel][None, :]
     num = np.where(np.abs(terms) > eps2, terms, 0.0).sum(axis=1)
     e_pt2 = float(np.sum(num * num / (e_var - diag[out])))
-    return HBCIResult(e_var, e_pt2, e_var + e_pt2, int(sel.sum()), rounds, sel, c)
+    return HBCIResult(e_var, e_pt2, e_var + e_pt2, int(sel.sum()), rounds, sel, c, margin1)
 
 
 def spin_flip_permutation(nstr: int) -> np.ndarray:

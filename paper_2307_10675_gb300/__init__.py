@@ -10,5 +10,5 @@ from .api import (  # noqa: F401
     ifci_build_strings, ifci_davidson_batched, ifci_frozen_core, ifci_h_elements, ifci_hdiag, ifci_increments,
     ifci_num_subsets, ifci_rdm_backward, ifci_sigma, ifci_sigma_noalloc, ifci_sigma_noalloc_max_bytes,
     ifci_wait_selftest,
-    ifci_string_counts,
+    ifci_string_counts, ifci_hbci_batched, reference_determinant,
 )

@@ -30,6 +30,7 @@ EXPORTS = [
     "ifci_frozen_core", "ifci_davidson_default_opts", "ifci_davidson_batched", "ifci_num_subsets",
     "ifci_increments", "ifci_rdm_backward", "ifci_profile_enable", "ifci_profile_read",
     "ifci_sigma_noalloc", "ifci_sigma_noalloc_max_bytes", "ifci_h_elements", "ifci_wait_selftest",
+    "ifci_hbci_batched",
 ]
 PROFILE_KINDS = {"gather": 0, "contract": 1, "scatter": 2, "vector": 3, "other": 4, "contract_hi": 5}
 
@@ -53,7 +54,12 @@ class DavidsonOpts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("max_iter", c_int), ("max_space", c_int), ("e_tol", c_double),
                 ("r_tol", c_double), ("refine", c_int), ("hi_precision", c_int), ("det_budget", c_ll),
                 ("graph_iters", c_int), ("sector_passes", c_int), ("decouple_tol", c_double),
-                ("cnb_threshold", c_double)]
+                ("cnb_threshold", c_double), ("hbci_max_rounds", c_int), ("hbci_eps1", c_double),
+                ("hbci_eps2", c_double)]
+
+
+class HbciOpts(ctypes.Structure):
+    _fields_ = [("eps1", c_double), ("eps2", c_double), ("max_rounds", c_int)]
 
 
 def lib_path() -> str:
@@ -92,6 +98,9 @@ def load(build_if_missing: bool = True):
     L.ifci_davidson_default_opts.restype = None
     L.ifci_davidson_batched.argtypes = [H, c_int, ctypes.POINTER(Problem), ctypes.POINTER(DavidsonOpts),
                                         c_double_p, c_int_p, c_int_p, c_void_p]
+    L.ifci_hbci_batched.argtypes = [H, c_int, ctypes.POINTER(Problem), ctypes.POINTER(c_ll),
+                                    ctypes.POINTER(DavidsonOpts), ctypes.POINTER(HbciOpts), c_double_p, c_double_p,
+                                    ctypes.POINTER(c_ll), c_int_p, c_int_p, c_void_p]
     L.ifci_num_subsets.argtypes = [c_int, c_int, ctypes.POINTER(c_ll)]
     L.ifci_increments.argtypes = [H, ctypes.POINTER(System), c_int, ctypes.POINTER(DavidsonOpts), c_double_p,
                                   c_double_p, c_double_p, c_double_p, c_int_p, c_int_p, c_void_p]

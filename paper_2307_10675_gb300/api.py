@@ -275,6 +275,50 @@ def ifci_davidson_batched(handle: Handle, problems: List[CIProblem], opts=None, 
     return e, it, st
 
 
+def ifci_hbci_batched(handle: Handle, problems: List[CIProblem], start_dets, eps1: float = 1e-3, eps2: float = 1e-6,
+                      max_rounds: int = 50, opts=None, stream=None, allow_unconverged=False):
+    """Heat-bath selected CI + EN-PT2 per problem (include/ifci.h).  Returns a
+    dict of e_var, e_pt2, e_hbci (= e_var + e_pt2), nsel, rounds, status."""
+    n = len(problems)
+    arr = (_capi.Problem * max(n, 1))()
+    for i, p in enumerate(problems):
+        arr[i] = _capi.Problem(p.norb, p.nelec_spin, p.h1.data_ptr(), p.eri.data_ptr(), float(p.e_core),
+                               p.c_out.data_ptr() if p.c_out is not None else None)
+    start = np.ascontiguousarray(np.asarray(start_dets, dtype=np.int64).reshape(-1))
+    if start.size != n:
+        raise ValueError("one start determinant per problem")
+    ev, e2 = np.zeros(n), np.zeros(n)
+    nsel = np.zeros(n, dtype=np.int64)
+    rounds = np.zeros(n, dtype=np.int32)
+    st = np.zeros(n, dtype=np.int32)
+    o = opts or davidson_opts(IFCI_FP64E)
+    hb = _capi.HbciOpts(float(eps1), float(eps2), int(max_rounds))
+    rc = _lib().ifci_hbci_batched(handle.ptr, n, arr, start.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                  ctypes.byref(o), ctypes.byref(hb), ev.ctypes.data_as(_capi.c_double_p),
+                                  e2.ctypes.data_as(_capi.c_double_p),
+                                  nsel.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                  rounds.ctypes.data_as(_capi.c_int_p), st.ctypes.data_as(_capi.c_int_p),
+                                  _stream(stream))
+    handle.check(rc, allow=(IFCI_ERR_NOT_CONVERGED,) if allow_unconverged else ())
+    return {"e_var": ev, "e_pt2": e2, "e_hbci": ev + e2, "nsel": nsel, "rounds": rounds, "status": st}
+
+
+def reference_determinant(body_sizes, X) -> int:
+    """Index I = Ia * nstr + Ia of the determinant with every bonding orbital of
+    the body set X doubly occupied (each body's first orbital; X's orbitals in
+    body order, strings ranked by increasing bit mask)."""
+    import math
+    X = sorted(X)
+    bonding, off = [], 0
+    for b in X:
+        bonding.append(off)
+        off += int(body_sizes[b])
+    m = len(X)
+    ra = sum(math.comb(p, k + 1) for k, p in enumerate(bonding))
+    nstr = math.comb(off, m)
+    return ra * nstr + ra
+
+
 def ifci_num_subsets(nbody: int, max_order: int) -> int:
     c = ctypes.c_longlong()
     rc = _lib().ifci_num_subsets(nbody, max_order, ctypes.byref(c))

@@ -43,14 +43,17 @@ int ifci_sigma(ifci_handle_t h, const ifci_strings_t *str, const double *h1, con
     const bool sym = sym_req && (tc || oz) && 2 * ndet < (1ll << 31);
     p.sym = sym ? 1 : 0;   // the pair map is placed below, before the plan is uploaded
     plan.probs.push_back(p);
-    IFCI_TRY(plan_sigma(h, plan, sigma_elems(np, ndet), precision));
+    // one wave; a spin-symmetric FP64E problem above 2^31 G elements runs in row slabs
+    const long long whole = sigma_elems(np, ndet);
+    IFCI_TRY(plan_sigma(h, plan, (oz && sym) ? std::min(whole, kSigmaSlabBudget) : whole, precision));
     const size_t eb = sigma_elem_bytes(precision);
+    const long long delems_D = std::max(plan.max_delems, plan.max_qelems);
     size_t need = ws_round(sizeof(FoldDesc)) + ws_round((size_t)ld * ld * 8) + ws_round((size_t)ld * ld * 4) +
                   (tc ? ws_round((size_t)tc_operand_bytes(np, precision)) : 0) +
                   (oz ? ws_round((size_t)oz_operand_bytes(np)) + ws_round(8) : 0) +
                   ((tc || oz) ? ws_round((size_t)nstr * kBlk16Stride) : 0) +
                   (sym ? ws_round((size_t)nstr * pmap_ld(np) * 4) : 0) + plan_device_bytes(plan) +
-                  2 * ws_round((size_t)plan.max_delems * eb);
+                  ws_round((size_t)delems_D * eb) + ws_round((size_t)plan.max_delems * eb);
     IFCI_TRY(ws_reserve(h, need));
     auto *fd = ws_take<FoldDesc>(h, 1);
     double *W = ws_take<double>(h, (size_t)ld * ld);
@@ -79,7 +82,7 @@ int ifci_sigma(ifci_handle_t h, const ifci_strings_t *str, const double *h1, con
         IFCI_TRY(launch_oz_pack_w(h, 1, plan.d_probs, s));
         IFCI_TRY(launch_oz_dscale(h, plan.d_probs, c, ndet, s));
     }
-    void *D = ws_take<char>(h, (size_t)plan.max_delems * eb);
+    void *D = ws_take<char>(h, (size_t)delems_D * eb);
     void *G = ws_take<char>(h, (size_t)plan.max_delems * eb);
     if (!D || !G) return set_error(h, IFCI_ERR_OOM, "ifci_sigma: workspace");
     return run_sigma(h, plan, precision, D, G, s);

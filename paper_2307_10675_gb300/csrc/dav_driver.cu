@@ -63,17 +63,6 @@ struct Carver {
     }
 };
 
-std::vector<uint32_t> host_strings(int n, int m) {
-    std::vector<uint32_t> out;
-    uint64_t v = (1ull << m) - 1ull;
-    const uint64_t lim = 1ull << n;
-    while (v < lim) {
-        out.push_back((uint32_t)v);
-        const uint64_t t = v | (v - 1);
-        v = (t + 1) | (((~t & (t + 1)) - 1) >> (__builtin_ctzll(v) + 1));
-    }
-    return out;
-}
 
 // Runs one batch of units and their problems to convergence.  Problem
 // results land in hs (DavState per problem); blk (optional) gets the two
@@ -132,12 +121,14 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
             hw_prob.push_back(u);
             hw_start.push_back(s0);
         }
-        max_pd = std::max(max_pd, sigma_elems(np, ndet));
-        sum_pd += sigma_elems(np, ndet);
         SigmaProb sp{};
         sp.n = p.n; sp.nstr = nstr; sp.nexc = nexc; sp.np = np; sp.ld = np;
         sp.ndet = ndet; sp.stride = ndet;
         sp.sym = ((tc || oz) && 2ll * nstr * nstr < (1ll << 31)) ? 1 : 0;   // plan_sigma keeps it for tensor cores
+        // a spin-symmetric FP64E problem above the budget runs in row slabs of
+        // G; any other must fit one wave whole
+        if (!(oz && !lo && sp.sym)) max_pd = std::max(max_pd, sigma_elems(np, ndet));
+        sum_pd += sigma_elems(np, ndet);
         sp.dscale = 2.0;   // basis vectors are normalised: |D| <= 2
         hi.probs.push_back(sp);
         lop.probs.push_back(sp);
@@ -263,7 +254,10 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
         m.hwp = c.take<int>(hw_prob.size());
         m.hws = c.take<long long>(hw_start.size());
         m.dst = c.take<double *>(n);
-        m.D = c.take<char>((size_t)budget * 8);
+        // D holds the gathered intermediate on the CUDA-core paths, only the
+        // quantised copies of c on the FP64-emulating one
+        m.D = c.take<char>((size_t)((hi_prec == IFCI_FP64E && !lo) ? std::max(hi.max_qelems, 1ll)
+                                                                     : std::max(budget, hi.max_qelems)) * 8);
         m.G = c.take<char>((size_t)budget * 8);
         m.hi_p = c.take<SigmaProb>(hi.probs.size());
         m.hi_i = c.take<WorkItem>(hi.items.size());
@@ -364,6 +358,7 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
         dp.hd = mem.hd[i];
         dp.c_out = U.sector ? mem.cblk[i] : p.c_out;
         dp.seed = U.seed;
+        dp.mask = U.sector ? nullptr : p.mask;
         dp.gc = U.sector ? mem.gc[bs.unit] : nullptr;
         dp.gs = U.sector ? mem.gs[bs.unit] : nullptr;
         dp.e_core = p.e_core;
@@ -383,7 +378,11 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
     b.d_uhi = mem.uhi;
     b.d_ulo = mem.ulo;
     b.any_sector = false;
-    for (const Unit &U : units) b.any_sector = b.any_sector || U.sector;
+    b.any_mask = false;
+    for (const Unit &U : units) {
+        b.any_sector = b.any_sector || U.sector;
+        b.any_mask = b.any_mask || (!U.sector && U.spec.mask);
+    }
     hi.d_probs = mem.hi_p; hi.d_items = mem.hi_i; hi.d_tiles = mem.hi_t; hi.d_tctiles = mem.hi_c;
     IFCI_TRY(upload_plan_to(h, hi, s));
     if (lo) {
@@ -463,6 +462,19 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
 
 }  // namespace
 
+// Every m-electron string of n orbitals, ascending as bit masks.
+std::vector<uint32_t> host_strings(int n, int m) {
+    std::vector<uint32_t> out;
+    uint64_t v = (1ull << m) - 1ull;
+    const uint64_t lim = 1ull << n;
+    while (v < lim) {
+        out.push_back((uint32_t)v);
+        const uint64_t t = v | (v - 1);
+        v = (t + 1) | (((~t & (t + 1)) - 1) >> (__builtin_ctzll(v) + 1));
+    }
+    return out;
+}
+
 int hi_precision_of(const ifci_davidson_opts_t &o) {
     if (o.precision == IFCI_FP64) return IFCI_FP64;
     if (o.precision == IFCI_FP64E) return IFCI_FP64E;
@@ -481,6 +493,8 @@ int check_opts(ifci_handle_t h, const ifci_davidson_opts_t &o) {
     if (o.max_iter < 1) return set_error(h, IFCI_ERR_INVALID_ARG, "davidson: max_iter %d", o.max_iter);
     if (!(o.e_tol > 0) || !(o.r_tol > 0)) return set_error(h, IFCI_ERR_INVALID_ARG, "davidson: tolerances");
     if (!(o.decouple_tol >= 0)) return set_error(h, IFCI_ERR_INVALID_ARG, "davidson: decouple_tol");
+    if (o.hbci_max_rounds < 0 || !(o.hbci_eps1 >= 0) || !(o.hbci_eps2 >= 0))
+        return set_error(h, IFCI_ERR_INVALID_ARG, "davidson: hbci_max_rounds >= 0, hbci_eps1/2 >= 0 required");
     return IFCI_OK;
 }
 
@@ -517,8 +531,8 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
     for (int i = 0; i < nspec; i++) {
         const ProbSpec &p = specs[i];
         const int nstr = (int)binom(p.n, p.m);
-        Unit U{p, p.h1, p.eri, false, nullptr, (int)blocks.size(), 1, nullptr};
-        if (ngroup[i] > 1 && ngroup[i] <= 16 && p.m >= 1) {
+        Unit U{p, p.h1, p.eri, false, p.seed, (int)blocks.size(), 1, nullptr};
+        if (ngroup[i] > 1 && ngroup[i] <= 16 && p.m >= 1 && !p.mask) {
             // class of a string = electrons per group, 4 bits per group
             std::vector<uint32_t> gmask(ngroup[i], 0u);
             for (int q = 0; q < p.n; q++) gmask[label[i][q]] |= 1u << q;
@@ -567,7 +581,7 @@ int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_da
             bs.sym = 1;
             bs.sa_off = bs.sb_off = -1;
             bs.ndet = (long long)nstr * nstr;
-            bs.ndim = (long long)nstr * (nstr + 1) / 2;
+            bs.ndim = p.ndim > 0 ? p.ndim : (long long)nstr * (nstr + 1) / 2;
             blocks.push_back(bs);
         }
         units.push_back(U);
@@ -788,6 +802,10 @@ void ifci_davidson_default_opts(ifci_davidson_opts_t *o) {
     o->graph_iters = 0;
     o->sector_passes = 0;
     o->decouple_tol = 1e-5;
+    o->cnb_threshold = 0.0;
+    o->hbci_max_rounds = 0;
+    o->hbci_eps1 = 1e-3;
+    o->hbci_eps2 = 1e-6;
 }
 
 int ifci_davidson_batched(ifci_handle_t h, int nprob, const ifci_problem_t *probs, const ifci_davidson_opts_t *opts,

@@ -13,6 +13,13 @@ struct ProbSpec {
     double *c_out;          // device nstr*nstr or nullptr
     int seed_block = 0;     // 0: the default start block; r >= 1: start from the lowest vector of the
                             // r-th lowest decoupled block of the P-space matrix
+    // selected-CI iteration (hbci.cu): start from `seed` (normalised, zero
+    // outside the selection) and keep every vector on the determinants with
+    // mask[I] != 0 (sigma is zeroed elsewhere); ndim = dimension of the
+    // spin-flip-even vectors on the selection.  Needs decouple_tol = 0.
+    const double *seed = nullptr;
+    const unsigned char *mask = nullptr;
+    long long ndim = 0;
 };
 
 // coupling graph of one problem's orbitals (sectors.cu)
@@ -29,6 +36,8 @@ struct MaskDesc {
     unsigned char label[32];   // group of each orbital
 };
 
+// Every m-electron string of n orbitals, ascending as bit masks (host).
+std::vector<uint32_t> host_strings(int n, int m);
 int check_opts(ifci_handle_t h, const ifci_davidson_opts_t &o);
 int hi_precision_of(const ifci_davidson_opts_t &o);   // precision of the exact (restart) sigma
 // Solves every problem; its memory comes from the handle's Davidson workspace
@@ -36,6 +45,10 @@ int hi_precision_of(const ifci_davidson_opts_t &o);   // precision of the exact 
 // energies).  Synchronous.
 int dav_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o, double *energies,
               int *iters, int *status, cudaStream_t s, double *blk_energy = nullptr);
+// HBCI of every problem from its closed-shell start determinant (hbci.cu)
+int hbci_solve(ifci_handle_t h, const std::vector<ProbSpec> &specs, const std::vector<long long> &start,
+               const ifci_davidson_opts_t &o, const ifci_hbci_opts_t &hb, double *e_var, double *e_pt2,
+               long long *nsel, int *rounds, int *status, cudaStream_t s);
 // dav_solve, then (opts.sector_passes >= 2) a second pass over the problems
 // whose P-space shows a competitive second block.
 int dav_solve_sectors(ifci_handle_t h, const std::vector<ProbSpec> &specs, const ifci_davidson_opts_t &o,

@@ -26,6 +26,7 @@ struct DavProb {
     double *c_out;           // converged vector or nullptr
     const double *seed;      // start vector (ndet, normalised) instead of the start block, or nullptr
     double *gc, *gs;         // sector blocks: the whole space's sigma input / output (nstr^2) or nullptr
+    const unsigned char *mask;   // selected-CI problem: determinants kept (sigma zeroed elsewhere) or nullptr
     double e_core;
 };
 
@@ -124,6 +125,7 @@ struct DavBatch {
     // sigma units (one CI space each; a sectored space has several problems)
     int nunit = 0;
     bool any_sector = false;
+    bool any_mask = false;        // some problem iterates on a determinant selection (DavProb::mask)
     int2 *d_urange = nullptr;     // [nunit] first problem, problem count
     long long *d_pidx = nullptr;  // [nprob][kPspMax] P-space determinants of the start block
     int *d_pcount = nullptr;      // [nprob]

@@ -95,8 +95,8 @@ int ifci_increments(ifci_handle_t h, const ifci_system_t *sys, int max_order, co
         if (P.nA[x] > kMaxNorb || binom(P.nA[x], (int)P.subsets[x].size()) >= kMaxStr)
             return set_error(h, IFCI_ERR_INVALID_ARG, "increments: body set %d has %d active orbitals", x, P.nA[x]);
 
-    // keep the converged vectors for the backward pass
-    const bool keep = o.refine >= 0;
+    // keep the converged vectors for the backward pass (exact CI only)
+    const bool keep = o.refine >= 0 && o.hbci_max_rounds == 0;
     std::vector<long long> vec_off(ns + 1, 0);
     for (int x = 0; x < ns; x++) {
         long long nstr = binom(P.nA[x], (int)P.subsets[x].size());
@@ -200,7 +200,30 @@ int ifci_increments(ifci_handle_t h, const ifci_system_t *sys, int max_order, co
                 }
                 std::vector<double> e(sp.size());
                 std::vector<int> it(sp.size()), stt(sp.size());
-                const int r = dav_solve_sectors(h, sp, o, e.data(), it.data(), stt.data(), s);
+                int r;
+                if (o.hbci_max_rounds > 0) {
+                    // HBCI from the reference determinant of X: every bonding
+                    // orbital (each body's first) doubly occupied; X's orbitals
+                    // in body order, strings ranked by increasing bit mask
+                    std::vector<long long> start;
+                    for (size_t t = first; t < j; t++) {
+                        const std::vector<int> &X = P.subsets[xs[t]];
+                        long long rank = 0;
+                        int off = 0;
+                        for (size_t k = 0; k < X.size(); k++) {
+                            rank += binom(off, (int)k + 1);
+                            off += sys->body_offset[X[k] + 1] - sys->body_offset[X[k]];
+                        }
+                        const long long nstr = binom(P.nA[xs[t]], (int)X.size());
+                        start.push_back(rank * nstr + rank);
+                    }
+                    const ifci_hbci_opts_t hb{o.hbci_eps1, o.hbci_eps2, o.hbci_max_rounds};
+                    std::vector<double> e2(sp.size());
+                    r = hbci_solve(h, sp, start, o, hb, e.data(), e2.data(), nullptr, it.data(), stt.data(), s);
+                    for (size_t t = 0; t < sp.size(); t++) e[t] += e2[t];
+                } else {
+                    r = dav_solve_sectors(h, sp, o, e.data(), it.data(), stt.data(), s);
+                }
                 if (r != IFCI_OK && r != IFCI_ERR_NOT_CONVERGED) return r;
                 if (r != IFCI_OK) ret = r;
                 for (size_t t = first; t < j; t++) {

@@ -254,6 +254,8 @@ extern "C" int ifci_rdm_backward(ifci_handle_t h, const ifci_system_t *sys, int 
     if (!h) return IFCI_ERR_INVALID_ARG;
     IFCI_TRY(validate_system(h, sys, max_order));
     if (!dh || !deri) return set_error(h, IFCI_ERR_INVALID_ARG, "rdm_backward: null output");
+    if (opts && opts->hbci_max_rounds > 0)
+        return set_error(h, IFCI_ERR_UNSUPPORTED, "rdm_backward: no gradient of the HBCI energy (its PT2 part)");
     IFCI_CUDA_TRY(h, cudaSetDevice(h->device));
     cudaStream_t s = as_cuda(stream);
     const int norb = sys->norb;

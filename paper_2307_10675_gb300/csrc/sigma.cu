@@ -240,21 +240,69 @@ int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision
     plan.tiles.clear();
     plan.tctiles.clear();
     plan.max_delems = 0;
+    plan.max_qelems = 0;
     const bool tc = precision == IFCI_BF16 || precision == IFCI_TF32;
-    SigmaWave w{0, 0, 0, 0, 0, 0, 0, 0};
+    SigmaWave w{};
+    auto close_wave = [&](int next_prob) {
+        if (w.nprob) {
+            plan.max_delems = std::max(plan.max_delems, w.delems);
+            plan.max_qelems = std::max(plan.max_qelems, w.qelems);
+            plan.waves.push_back(w);
+        }
+        w = SigmaWave{};
+        w.prob0 = next_prob;
+        w.item0 = (int)plan.items.size();
+        w.tile0 = (int)plan.tiles.size();
+        w.tc0 = (int)plan.tctiles.size();
+    };
     for (size_t i = 0; i < plan.probs.size(); i++) {
         SigmaProb &p = plan.probs[i];
         // the alpha-only form is a tensor-core gather; the CUDA-core paths build the full D
         p.sym = (p.sym && (tc || precision == IFCI_FP64E) && 2 * p.ndet < (1ll << 31)) ? 1 : 0;
         long long need = sigma_elems(p.np, p.ndet);
+        if (need > budget && precision == IFCI_FP64E && p.sym) {
+            // row slabs of G: each its own wave, the scatter accumulating into S
+            if (p.npc <= 0 || !p.act) p.npc = p.np;
+            const int rpt = tcg::rows_per_tile(p.nstr);
+            const long long row_elems = (long long)p.np * p.nstr;
+            int rows = (int)std::min<long long>(p.nstr, budget / row_elems);
+            rows = rows / rpt * rpt;
+            if (rows < 1)
+                return set_error(h, IFCI_ERR_OOM, "sigma: one alpha row block needs %lld intermediate elements, "
+                                 "budget %lld", row_elems * rpt, budget);
+            close_wave((int)i);
+            const int nchunk = (((p.npc + 63) / 64) + 2) / 3;
+            for (int r0 = 0; r0 < p.nstr; r0 += rows) {
+                const int r1 = std::min(p.nstr, r0 + rows);
+                w.nprob = 1;
+                p.doff = 0;
+                p.qoff = 0;
+                w.delems = (long long)p.np * (r1 - r0) * p.nstr;
+                w.qelems = 3 * p.ndet;   // +-Q and the int64 accumulator S
+                w.k0 = (long long)r0 * p.nstr;
+                w.kn = (long long)(r1 - r0) * p.nstr;
+                w.slab_first = r0 == 0;
+                w.slab_last = r1 == p.nstr;
+                for (long long s0 = 0; s0 < p.ndet; s0 += kGatherChunk) {
+                    plan.items.push_back(WorkItem{(int)i, 0, s0});
+                    w.nitem++;
+                }
+                for (int n0 = 0; n0 < p.npc; n0 += oz_tile_n())
+                    for (int kc = 0; kc < nchunk; kc++) {
+                        size_t before = plan.tctiles.size();
+                        tcg::append_row_tiles(plan.tctiles, (int)i, n0 | (kc << 16), p.nstr, r0, r1);
+                        w.ntc += (int)(plan.tctiles.size() - before);
+                    }
+                close_wave((int)i);
+            }
+            w.prob0 = (int)i + 1;
+            continue;
+        }
         if (need > budget)
             return set_error(h, IFCI_ERR_OOM, "sigma: one problem needs %lld intermediate elements, budget %lld",
                              need, budget);
-        if (w.delems + need > budget) {
-            plan.max_delems = std::max(plan.max_delems, w.delems);
-            plan.waves.push_back(w);
-            w = SigmaWave{(int)plan.items.size(), 0, (int)plan.tiles.size(), 0, (int)plan.tctiles.size(), 0, 0, 0};
-        }
+        if (w.delems + need > budget) close_wave((int)i);
+        w.nprob++;
         p.doff = w.delems;
         w.delems += need;
         p.qoff = w.qelems;
@@ -272,11 +320,14 @@ int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision
             // one tile = up to 128 determinants x oz_tile_n() output pairs (sigma_oz.cu);
             // the output-pair tiles of a problem run back to back so W stays resident longer
             if (p.npc <= 0 || !p.act) p.npc = p.np;
-            for (int n0 = 0; n0 < p.npc; n0 += oz_tile_n()) {
-                size_t before = plan.tctiles.size();
-                tcg::append_row_tiles(plan.tctiles, (int)i, n0, p.nstr);
-                w.ntc += (int)(plan.tctiles.size() - before);
-            }
+            // K chunks of 192 pairs keep every level sum exact (sigma_oz.cu)
+            const int nchunk = (((p.npc + 63) / 64) + 2) / 3;
+            for (int n0 = 0; n0 < p.npc; n0 += oz_tile_n())
+                for (int kc = 0; kc < nchunk; kc++) {
+                    size_t before = plan.tctiles.size();
+                    tcg::append_row_tiles(plan.tctiles, (int)i, n0 | (kc << 16), p.nstr);
+                    w.ntc += (int)(plan.tctiles.size() - before);
+                }
         } else {
             for (int m0 = 0; m0 < p.np; m0 += kGemmTM)
                 for (long long s0 = 0; s0 < p.ndet; s0 += kGemmTN) {
@@ -285,10 +336,7 @@ int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision
                 }
         }
     }
-    if (w.nitem) {
-        plan.max_delems = std::max(plan.max_delems, w.delems);
-        plan.waves.push_back(w);
-    }
+    close_wave((int)plan.probs.size());
     plan.any_sym = false;
     for (const SigmaProb &p : plan.probs) plan.any_sym = plan.any_sym || p.sym;
     // dynamically scheduled tensor-core tiles: largest problems first (longest
@@ -351,6 +399,52 @@ int upload_plan_to(ifci_handle_t h, SigmaPlan &plan, cudaStream_t s) {
     return IFCI_OK;
 }
 
+// The same for one row slab of a spin-flip-symmetric problem (SigmaWave::kn):
+// G holds alpha rows [r0, r1) only; the alpha loop takes the excitations whose
+// J row lies in the slab, the beta loop runs when I's own row does.  The sum
+// is carried in the int64 accumulator S across the slabs (exact, so the
+// result equals the unsplit scatter bit for bit) and converted on the last.
+__global__ void __launch_bounds__(kGatherChunk)
+scatter_fixed_slab_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__ items,
+                          const long long *__restrict__ G, long long *__restrict__ Qbuf, int r0, int r1, int first,
+                          int last) {
+    const WorkItem it = items[blockIdx.x];
+    const SigmaProb &p = probs[it.prob];
+    if (p.active && !*p.active) return;
+    const long long I = it.start + threadIdx.x;
+    if (I >= p.ndet) return;
+    const int nstr = p.nstr, nexc = p.nexc;
+    const long long kn = (long long)(r1 - r0) * nstr, k0 = (long long)r0 * nstr;
+    const int ia = (int)(I / nstr), ib = (int)(I % nstr);
+    const int32_t *__restrict__ ea = p.exc + (size_t)ia * nexc;
+    const uint8_t *__restrict__ pact = p.pact;
+    long long *S = Qbuf + p.qoff + 2 * p.ndet;
+    long long acc = first ? 0 : S[I];
+    for (int e = 0; e < nexc; e++) {
+        const int32_t x = ea[e];
+        const int J = exc_J(x);
+        if (J < r0 || J >= r1 || (pact && !pact[exc_pair(x)])) continue;
+        const long long gv = G[(long long)exc_pair(x) * kn + (long long)J * nstr + ib - k0];
+        acc += (x & 1) ? -gv : gv;
+    }
+    if (ia >= r0 && ia < r1) {
+        const int32_t *__restrict__ eb = p.exc + (size_t)ib * nexc;
+        const long long rowb = (long long)ia * nstr - k0;
+        for (int e = 0; e < nexc; e++) {
+            const int32_t x = eb[e];
+            if (pact && !pact[exc_pair(x)]) continue;
+            const long long gv = G[(long long)exc_pair(x) * kn + rowb + exc_J(x)];
+            acc += (x & 1) ? -gv : gv;
+        }
+    }
+    if (last) {
+        double *s = p.sbase + (p.sslot ? (long long)*p.sslot : 0ll) * p.stride;
+        s[I] = (double)acc * (p.Wexp[0] * p.dscale * 0x1p-45);
+    } else {
+        S[I] = acc;
+    }
+}
+
 int run_sigma(ifci_handle_t h, const SigmaPlan &plan, int precision, void *D, void *G, cudaStream_t s) {
     for (const SigmaWave &w : plan.waves) {
         if (w.nitem == 0) continue;
@@ -396,10 +490,17 @@ int run_sigma(ifci_handle_t h, const SigmaPlan &plan, int precision, void *D, vo
             }
             IFCI_TRY(launch_oz_contract(h, plan, w, D, G, s));
             ProfScope ps(h, s, PK_SCATTER);
-            scatter_fixed_kernel<<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
-                                                                  (const long long *)G);
+            if (w.kn) {
+                const int nstr = plan.probs[w.prob0].nstr;
+                scatter_fixed_slab_kernel<<<w.nitem, kGatherChunk, 0, s>>>(
+                    plan.d_probs, plan.d_items + w.item0, (const long long *)G, (long long *)D,
+                    (int)(w.k0 / nstr), (int)((w.k0 + w.kn) / nstr), w.slab_first, w.slab_last);
+            } else {
+                scatter_fixed_kernel<<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0,
+                                                                      (const long long *)G);
+            }
             IFCI_LAUNCH_CHECK(h);
-            if (plan.any_sym) {
+            if (plan.any_sym && (!w.kn || w.slab_last)) {
                 sym_sum_kernel<<<w.nitem, kGatherChunk, 0, s>>>(plan.d_probs, plan.d_items + w.item0);
                 IFCI_LAUNCH_CHECK(h);
             }

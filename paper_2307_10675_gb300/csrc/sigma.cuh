@@ -52,14 +52,23 @@ struct WorkItem {
 };
 
 constexpr int kGatherChunk = 256;   // determinants per gather/scatter block
+constexpr long long kSigmaSlabBudget = 1ll << 31;   // G elements per row slab of ifci_sigma (16 GB int64)
 constexpr int kGemmTM = 64, kGemmTN = 64, kGemmTK = 16;
 
 struct SigmaWave {
+    int prob0, nprob;        // problems of the wave (consecutive in the plan)
     int item0, nitem;        // gather/scatter items
     int tile0, ntile;        // contraction tiles
     int tc0, ntc;            // tensor-core tiles (BF16/TF32)
     long long delems;        // D (and G) elements of the wave
     long long qelems;        // elements of the quantised copies of c (sum of ndet)
+    // Row slab of one spin-flip-symmetric FP64E problem too large for the
+    // budget (kn > 0): G holds the determinants [k0, k0 + kn) only (whole alpha
+    // rows), G[A][K - k0] with row stride kn; the scatter adds the slab's
+    // contributions into an int64 accumulator S (after the problem's +-Q copy
+    // in the D buffer) and converts on the last slab.  kn = 0: whole problems.
+    long long k0, kn;
+    int slab_first, slab_last;
 };
 
 // Host-side plan over a fixed problem set; device arrays live in caller memory.
@@ -68,13 +77,16 @@ struct SigmaPlan {
     std::vector<SigmaWave> waves;
     std::vector<WorkItem> items, tiles, tctiles;
     long long max_delems = 0;
+    long long max_qelems = 0;   // largest quantised copy of a wave (the D buffer of the FP64E path)
     bool any_sym = false;    // some problem uses the spin-flip-symmetric gathers
     SigmaProb *d_probs = nullptr;
     WorkItem *d_items = nullptr, *d_tiles = nullptr, *d_tctiles = nullptr;
 };
 
 // Splits probs into waves of at most `budget` D elements (each problem whole).
-// Fails if one problem alone exceeds the budget.
+// A problem alone above the budget is split into row slabs (SigmaWave::kn)
+// when it takes the spin-flip-symmetric FP64E path; otherwise it fails with
+// IFCI_ERR_OOM.
 int plan_sigma(ifci_handle_t h, SigmaPlan &plan, long long budget, int precision);
 size_t plan_device_bytes(const SigmaPlan &plan);
 // Copies the plan's descriptor arrays to device memory taken from the workspace.

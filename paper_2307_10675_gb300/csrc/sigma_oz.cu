@@ -14,7 +14,9 @@
 // and one packed FP16 subtraction: no FP64 arithmetic in this kernel.
 // The product of two slices over K <= 204 terms stays below 2^24 even when the (up to five)
 // slice pairs of one scale level L = i + j share an accumulator, so each level
-// is summed exactly by the tensor cores in FP32.  The 15 slice pairs with
+// is summed exactly by the tensor cores in FP32; a problem with more pairs is
+// split into K chunks of 192 pairs, each its own tile, whose int64 partial
+// sums are added into G (exact, in any order).  The 15 slice pairs with
 // i + j <= 4 (0-based) are kept; the epilogue combines the five levels exactly
 // in int64, G = 2^-45 Wscale dscale sum_L 2^{8 (4 - L)} acc_L, and stores the
 // integer; the scatter sums those integers and converts once per determinant
@@ -45,7 +47,8 @@ constexpr int kS = 5;                       // slices per operand
 constexpr int kNT = 96;                     // output pairs per tile
 constexpr int kThreads = 512;               // 4 threads per determinant row
 constexpr int kOzTmemCols = 512;
-constexpr int kMaxNpExact = 204;            // exact level sums need npair <= 204
+constexpr int kMaxNpExact = 204;            // exact level sums need at most 204 pairs per K chunk
+constexpr int kMaxNpTable = 304;            // 16-pair block offsets per string (kBlk16Stride) cover 304 pairs
 constexpr size_t kWStage = (size_t)kS * kNT * kAtomBytes;     // 61,440 B
 constexpr size_t kAStage = (size_t)kS * kTM * kAtomBytes;     // 81,920 B
 constexpr long long kDigitBias = 128ll * 0x0101010101ll;      // 128 in each of the five digits
@@ -81,18 +84,28 @@ __device__ __forceinline__ uint32_t digit_pair_f16(uint32_t a, uint32_t b, int D
     return *reinterpret_cast<uint32_t *>(&v);
 }
 
-__device__ __forceinline__ const uint8_t *stage_src(const SigmaProb *probs, const WorkItem *tiles, int t, int a) {
+// A tile's sub field: its first output pair (low 16 bits) and its K chunk (the
+// atoms [kChunkAtoms kc, kChunkAtoms (kc + 1)), so that every level sum of a
+// chunk stays an exact integer below 2^24 whatever npair is)
+constexpr int kChunkAtoms = 3;   // 192 pairs per chunk
+static_assert(kChunkAtoms * 64 <= kMaxNpExact, "a K chunk must keep its level sums exact");
+__host__ __device__ inline int tile_n0(int sub) { return sub & 0xFFFF; }
+__host__ __device__ inline int tile_kc(int sub) { return sub >> 16; }
+
+// W stage of local atom la of tile t
+__device__ __forceinline__ const uint8_t *stage_src(const SigmaProb *probs, const WorkItem *tiles, int t, int la) {
     const WorkItem tile = tiles[t];
     const SigmaProb &p = probs[tile.prob];
-    const int KA = k_atoms(p.act ? p.npc : p.np), nt = tile.sub / kNT;
-    return (const uint8_t *)p.Woz + ((size_t)nt * KA + a) * kWStage;
+    const int KA = k_atoms(p.act ? p.npc : p.np), nt = tile_n0(tile.sub) / kNT;
+    return (const uint8_t *)p.Woz + ((size_t)nt * KA + kChunkAtoms * tile_kc(tile.sub) + la) * kWStage;
 }
 
-// G[A][K] (int64, fixed point 2^-45 Wscale dscale) for one tile of 128 determinants x 96 pairs.
+// G[A][K] (int64, fixed point 2^-45 Wscale dscale) for one tile of 128 determinants x 96 pairs;
+// for a row slab (kn > 0) G[A][K - k0] with row stride kn.
 __global__ void __launch_bounds__(kThreads, 1)
 oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restrict__ tiles, int ntile,
                    const long long *__restrict__ Q, long long *__restrict__ G, int *__restrict__ err,
-                   int *__restrict__ counter) {
+                   int *__restrict__ counter, long long k0, long long kn) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_w[2], bar_mma;
     __shared__ uint32_t tmem_slot;
@@ -141,11 +154,14 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
         const SigmaProb &pg = probs[tile.prob];
         // np: the pairs contracted (a sectored space: its active pairs, in compact order)
         const int np = pg.act ? pg.npc : pg.np, nstr = pg.nstr, sym = pg.sym;
-        const long long ndet = pg.ndet, doff = pg.doff;
+        // G row stride: the problem's determinants, or those of its row slab [k0, k0 + kn)
+        const long long gld = kn ? kn : pg.ndet, doff = pg.doff;
         const int32_t *pmap = pg.act ? pg.pmapc : pg.pmap;
         const int32_t *act = pg.act;
         const long long *C = Q + pg.qoff;   // round(c 2^38 / dscale) (and its negation when sym)
-        const int KA = k_atoms(np), n0 = tile.sub;
+        const int KA = k_atoms(np), n0 = tile_n0(tile.sub);
+        const int a0 = kChunkAtoms * tile_kc(tile.sub), a1 = min(KA, a0 + kChunkAtoms);
+        const bool chunked = KA > kChunkAtoms;   // partial sums: added to G (zeroed before the launch)
         const int Nt = round_up(min(kNT, np - n0), 16);
         const tcg::TileGeom geo = tcg::tile_geom(tile.start, nstr);
         const bool live = row < geo.R * geo.Cw;
@@ -153,8 +169,8 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
         const int ka = geo.ka0 + r, kb = geo.kb0 + (live ? row % geo.Cw : 0);
         const long long K = (long long)ka * nstr + kb;
         int4 pmn[4];               // pair-map row of this thread's next block
-        if (sym && live) tcg::pmap_load16(pmap, np, ka, q, pmn);
-        for (int a = 0; a < KA; a++, g++) {
+        if (sym && live) tcg::pmap_load16(pmap, np, ka, 4 * a0 + q, pmn);
+        for (int a = a0; a < a1; a++, g++) {
             // ---- loads of this atom's block (pairs 64a + 16q .. + 16): they overlap
             // the MMAs of the previous atom, which are still running
             const int b = 4 * a + q;
@@ -166,7 +182,7 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
                     int4 pmc[4];
 #pragma unroll
                     for (int u = 0; u < 4; u++) pmc[u] = pmn[u];
-                    if (a + 1 < KA) tcg::pmap_load16(pmap, np, ka, b + 4, pmn);
+                    if (a + 1 < a1) tcg::pmap_load16(pmap, np, ka, b + 4, pmn);
                     tcg::gather_pm16<long long>(C, kb, pmc, x);
                 } else {
                     tcg::gather_block16<long long>(probs[tile.prob], C, ka, kb, b, x);
@@ -174,13 +190,13 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
             }
             // MMAs of the previous atom done: A and W buffer (g + 1) & 1 are free
             // (thread 0 polls, the others wait at the barrier)
-            if (a > 0) {
+            if (a > a0) {
                 if (!__syncthreads_and(tid == 0 ? (ok && mbar_wait(bm, ph_m)) : 1)) { ok = false; break; }
                 ph_m ^= 1;
             }
             // prefetch the next W stage (thread 0 wrote s_next itself: no barrier needed to read it)
             if (tid == 0) {
-                const int nt2 = a + 1 < KA ? t : s_next, na = a + 1 < KA ? a + 1 : 0;
+                const int nt2 = a + 1 < a1 ? t : s_next, na = a + 1 < a1 ? a + 1 - a0 : 0;
                 if (nt2 < ntile)
                     bulk_load(smem_u32(Wsm0 + ((g + 1) & 1) * kWStage), stage_src(probs, tiles, nt2, na),
                               (uint32_t)kWStage, ((g + 1) & 1) ? bw1 : bw0);
@@ -229,7 +245,7 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
                                     mma_f16(tmem + (uint32_t)((i + j) * kNT),
                                             ad0 + (uint64_t)((j * kTM * kAtomBytes + ks * 32) >> 4),
                                             wd0 + (uint64_t)((i * kNT * kAtomBytes + ks * 32) >> 4), idesc,
-                                            (a > 0 || j > 0 || ks > 0) ? 1u : 0u);
+                                            (a > a0 || j > 0 || ks > 0) ? 1u : 0u);
                     mma_commit(bm);
                 }
             }
@@ -263,7 +279,11 @@ oz_contract_kernel(const SigmaProb *__restrict__ probs, const WorkItem *__restri
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
                     const int A = n0 + c0 + j;
-                    if (c0 + j < Nt && A < np) Gp[(long long)(act ? act[A] : A) * ndet + K] = gi[j];
+                    if (c0 + j < Nt && A < np) {
+                        long long *dst = Gp + (long long)(act ? act[A] : A) * gld + (K - k0);
+                        if (chunked) atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)gi[j]);
+                        else *dst = gi[j];
+                    }
                 }
             }
         }
@@ -374,8 +394,15 @@ int launch_oz_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &
                        cudaStream_t s) {
     if (w.ntc == 0) return IFCI_OK;
     for (const SigmaProb &p : plan.probs)
-        if ((p.act ? p.npc : p.np) > kMaxNpExact)
-            return set_error(h, IFCI_ERR_UNSUPPORTED, "FP64E: npair %d > %d (exact level sums)", p.np, kMaxNpExact);
+        if (p.np > kMaxNpTable)
+            return set_error(h, IFCI_ERR_UNSUPPORTED, "FP64E: npair %d > %d", p.np, kMaxNpTable);
+    // K chunks add their partial sums: zero those problems' G first
+    for (int i = w.prob0; i < w.prob0 + w.nprob; i++) {
+        const SigmaProb &p = plan.probs[i];
+        if (k_atoms(p.act ? p.npc : p.np) > kChunkAtoms)
+            IFCI_CUDA_TRY(h, cudaMemsetAsync(static_cast<long long *>(G) + p.doff, 0,
+                                             (size_t)p.np * (w.kn ? w.kn : p.ndet) * 8, s));
+    }
     if (!h->d_err || !h->d_counter) return set_error(h, IFCI_ERR_INVALID_ARG, "FP64E: no error flag / counter");
     const size_t smem = 1024 + 2 * kWStage + kAStage;   // 205,824 B
     static SmemOptIn opt;
@@ -384,7 +411,8 @@ int launch_oz_contract(ifci_handle_t h, const SigmaPlan &plan, const SigmaWave &
     IFCI_CUDA_TRY(h, cudaMemsetAsync(h->d_counter, 0, sizeof(int), s));
     ProfScope ps(h, s, PK_CONTRACT_HI);
     oz_contract_kernel<<<grid, kThreads, smem, s>>>(plan.d_probs, plan.d_tctiles + w.tc0, w.ntc,
-                                                    (const long long *)Q, (long long *)G, h->d_err, h->d_counter);
+                                                    (const long long *)Q, (long long *)G, h->d_err, h->d_counter,
+                                                    w.k0, w.kn);
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;
 }

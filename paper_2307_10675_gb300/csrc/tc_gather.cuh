@@ -40,16 +40,25 @@ __host__ __device__ inline TileGeom tile_geom(long long start, int nstr) {
     return g;
 }
 
-// Host: the row-aligned tiles of one problem, in order.
-inline void append_row_tiles(std::vector<WorkItem> &out, int prob, int sub, int nstr) {
+// Alpha rows one tile covers when a row is shorter than a tile (else 1).
+inline int rows_per_tile(int nstr) {
+    if (nstr >= kTileDets) return 1;
+    const int rmax = kTileDets / nstr;
+    return rmax > kRows ? kRows : rmax;
+}
+
+// Host: the row-aligned tiles of alpha rows [r0, r1) of one problem (all rows
+// when r1 < 0), in order; r0 and r1 are multiples of rows_per_tile(nstr)
+// (r1 may be nstr).
+inline void append_row_tiles(std::vector<WorkItem> &out, int prob, int sub, int nstr, int r0 = 0, int r1 = -1) {
+    if (r1 < 0) r1 = nstr;
     if (nstr >= kTileDets) {
-        for (int ka = 0; ka < nstr; ka++)
+        for (int ka = r0; ka < r1; ka++)
             for (int kb0 = 0; kb0 < nstr; kb0 += kTileDets)
                 out.push_back(WorkItem{prob, sub, (long long)ka * nstr + kb0});
     } else {
-        int rmax = kTileDets / nstr;
-        if (rmax > kRows) rmax = kRows;
-        for (int ka0 = 0; ka0 < nstr; ka0 += rmax) out.push_back(WorkItem{prob, sub, (long long)ka0 * nstr});
+        const int rmax = rows_per_tile(nstr);
+        for (int ka0 = r0; ka0 < r1; ka0 += rmax) out.push_back(WorkItem{prob, sub, (long long)ka0 * nstr});
     }
 }
 
@@ -83,6 +92,9 @@ namespace tcg {
 template <typename T>
 __device__ __forceinline__ void gather_block16(const SigmaProb &p, const T *__restrict__ c, int ka, int kb, int b,
                                                T (&x)[16]) {
+    // padding block of the last atom (its pairs are beyond np): nothing to add,
+    // and its end offset lies past the string's row of block offsets
+    if (16 * b >= p.np) return;
     const int nstr = p.nstr, nexc = p.nexc;
     const uint8_t *ba = p.blk + (size_t)ka * kBlk16Stride, *bb = p.blk + (size_t)kb * kBlk16Stride;
     const int a0 = ba[b], a1 = ba[b + 1], b0 = bb[b], b1 = bb[b + 1];

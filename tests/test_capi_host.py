@@ -81,7 +81,8 @@ def _header_struct_fields(name):
 
 
 @pytest.mark.parametrize("cname,pyname", [("ifci_davidson_opts_t", "DavidsonOpts"), ("ifci_problem_t", "Problem"),
-                                           ("ifci_system_t", "System"), ("ifci_strings_t", "Strings")])
+                                           ("ifci_system_t", "System"), ("ifci_strings_t", "Strings"),
+                                           ("ifci_hbci_opts_t", "HbciOpts")])
 def test_binding_structs_follow_the_header(cname, pyname):
     """The ctypes mirrors list the header's fields in the header's order."""
     from paper_2307_10675_gb300 import _capi
@@ -98,6 +99,8 @@ def test_davidson_default_opts_from_the_library():
     assert o.hi_precision == _capi.IFCI_FP64E
     assert o.det_budget == 0 and o.graph_iters == 0
     assert o.sector_passes == 0 and o.decouple_tol == 1e-5
+    assert o.cnb_threshold == 0.0
+    assert (o.hbci_max_rounds, o.hbci_eps1, o.hbci_eps2) == (0, 1e-3, 1e-6)
 
 
 def test_sigma_flag_matches_the_header():

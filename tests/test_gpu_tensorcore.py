@@ -1,4 +1,4 @@
-"""Tensor-core (tcgen05) BF16 sigma and the mixed-precision Davidson.
+"""Tensor-core (tcgen05) BF16 / TF32 sigma and the mixed-precision Davidson.
 
 Exactness test: with integrals and vectors on a coarse dyadic grid every
 operand of the contraction is exactly representable in BF16 and every
@@ -7,6 +7,9 @@ to FP64 rounding.  This pins the operand layouts (swizzle, descriptors,
 instruction shape) exactly.  With random inputs the BF16 sigma differs from
 the oracle by the BF16 input rounding (unit roundoff u = 2^-8): the test
 bounds the relative norm error by 4u and the max error by 16u * max|sigma|.
+TF32 (10 explicit mantissa bits, operands rounded with cvt.rna: u = 2^-11)
+takes the same tests with its own u; its W streams through two shared-memory
+stages, exercised up to npair 253 (n = 22).
 """
 import math
 
@@ -22,6 +25,7 @@ import paper_2307_10675_gb300 as ifci
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda", 0)
 U_BF16 = 2.0 ** -8
+U_TF32 = 2.0 ** -11
 
 
 @pytest.fixture(scope="module")
@@ -50,6 +54,41 @@ def test_bf16_sigma_exact_on_dyadic_inputs(handle, n, m):
     s16 = ifci.ifci_sigma(handle, t, h1, V, c, precision=ifci.IFCI_BF16)
     torch.cuda.synchronize()
     np.testing.assert_allclose(s16.cpu().numpy(), s64.cpu().numpy(), rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("n,m", [(6, 2), (10, 2), (14, 2), (18, 2), (8, 4), (21, 2), (22, 2)])
+def test_tf32_sigma_exact_on_dyadic_inputs(handle, n, m):
+    h1, V = _dyadic_problem(n, seed=n * 10 + m + 5)
+    t = ifci.ifci_build_strings(handle, n, m)
+    rng = np.random.default_rng(n + 5)
+    c = torch.tensor(rng.integers(-3, 4, size=t.nstr * t.nstr) / 4.0, device=DEV)
+    s64 = ifci.ifci_sigma(handle, t, h1, V, c, precision=ifci.IFCI_FP64)
+    s32 = ifci.ifci_sigma(handle, t, h1, V, c, precision=ifci.IFCI_TF32)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(s32.cpu().numpy(), s64.cpu().numpy(), rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("X", [(0,), (0, 1), (5, 7), (8, 11, 12), (2, 9, 16), "six"])
+def test_tf32_sigma_against_oracle(handle, X):
+    chain = chain_24_uneven()
+    if X == "six":
+        X = tuple(b for b, s in enumerate(chain.body_sizes) if s == 6)[:3]
+    sysa = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=DEV),
+                             torch.tensor(chain.eri_packed(), device=DEV))
+    h1, eri, ecore = ifci.ifci_frozen_core(handle, sysa, X)
+    t = ifci.ifci_build_strings(handle, h1.shape[0], len(X))
+    c = torch.tensor(random_ci_vector(t.nstr, t.nstr, seed=6), device=DEV)
+    sig = ifci.ifci_sigma(handle, t, h1, eri, c, precision=ifci.IFCI_TF32)
+    torch.cuda.synchronize()
+    cn = c.cpu().numpy().reshape(-1)
+    got = sig.cpu().numpy().reshape(-1)
+    if t.nstr * t.nstr <= 40000:
+        ref = fci.Hamiltonian(fci.subsystem(chain, X)).matvec(cn) - ecore * cn
+    else:   # CAS(6e,18o): the FP64 path, itself checked against oracle rows
+        ref = ifci.ifci_sigma(handle, t, h1, eri, c, precision=ifci.IFCI_FP64).cpu().numpy().reshape(-1)
+    err = got - ref
+    assert np.linalg.norm(err) <= 4 * U_TF32 * np.linalg.norm(ref)
+    assert np.max(np.abs(err)) <= 16 * U_TF32 * np.max(np.abs(ref))
 
 
 @pytest.mark.parametrize("X", [(0,), (0, 1), (5, 7), (8, 11, 12), (2, 9, 16)])
@@ -90,8 +129,10 @@ def test_bf16_sigma_full_size_matches_fp64_path(handle):
 
 # ---------------------------------------------------------------- FP64-accurate tensor-core contraction
 
-@pytest.mark.parametrize("n,m", [(6, 2), (14, 2), (18, 2), (8, 4)])
+@pytest.mark.parametrize("n,m", [(6, 2), (14, 2), (18, 2), (8, 4), (21, 2), (24, 2)])
 def test_fp64e_sigma_exact_on_dyadic_inputs(handle, n, m):
+    """npair 231 and 300 (n = 21, 24) run in K chunks of 192 pairs whose int64
+    partial sums are added into G: still exact."""
     h1, V = _dyadic_problem(n, seed=n * 10 + m + 1)
     t = ifci.ifci_build_strings(handle, n, m)
     rng = np.random.default_rng(n + 1)
@@ -132,7 +173,7 @@ def _symmetric(c, nstr):
     return ((m + m.T) / 2).reshape(-1).contiguous()
 
 
-@pytest.mark.parametrize("prec,atol", [("fp64e", 1e-12), ("bf16", 1e-9)])
+@pytest.mark.parametrize("prec,atol", [("fp64e", 1e-12), ("bf16", 1e-9), ("tf32", 1e-9)])
 @pytest.mark.parametrize("n,m", [(6, 2), (14, 2), (18, 2), (8, 4), (12, 4)])
 def test_symmetric_sigma_exact_on_dyadic_inputs(handle, prec, atol, n, m):
     """Alpha-only gather + S + S^T on a symmetric dyadic vector equals the FP64
@@ -147,6 +188,20 @@ def test_symmetric_sigma_exact_on_dyadic_inputs(handle, prec, atol, n, m):
     ss = ifci.ifci_sigma(handle, t, h1, V, c, precision=ifci.PRECISIONS[prec], spin_symmetric=True)
     torch.cuda.synchronize()
     np.testing.assert_allclose(ss.cpu().numpy(), s64.cpu().numpy(), rtol=0, atol=atol)
+
+
+@pytest.mark.parametrize("n,m", [(21, 2), (24, 2)])
+def test_symmetric_fp64e_sigma_exact_beyond_204_pairs(handle, n, m):
+    """The alpha-only FP64E path with K chunks (npair 231 and 300)."""
+    h1, V = _dyadic_problem(n, seed=n * 10 + m + 3)
+    t = ifci.ifci_build_strings(handle, n, m)
+    rng = np.random.default_rng(n + 3)
+    c = torch.tensor(rng.integers(-3, 4, size=t.nstr * t.nstr) / 8.0, device=DEV)
+    c = _symmetric(c, t.nstr)
+    s64 = ifci.ifci_sigma(handle, t, h1, V, c, precision=ifci.IFCI_FP64)
+    ss = ifci.ifci_sigma(handle, t, h1, V, c, precision=ifci.IFCI_FP64E, spin_symmetric=True)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(ss.cpu().numpy(), s64.cpu().numpy(), rtol=0, atol=1e-12)
 
 
 @pytest.mark.parametrize("X", [(0,), (0, 1), (5, 7), (8, 11, 12), "six"])
@@ -196,7 +251,7 @@ def test_symmetric_bf16_sigma_against_oracle(handle, X):
     assert np.max(np.abs(err)) <= 16 * U_BF16 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("prec,hi", [("fp64e", "fp64e"), ("bf16", "fp64e"), ("bf16", "fp64")])
+@pytest.mark.parametrize("prec,hi", [("fp64e", "fp64e"), ("bf16", "fp64e"), ("bf16", "fp64"), ("tf32", "fp64e")])
 def test_tensor_core_davidson_reaches_fp64_accuracy(handle, prec, hi):
     chain = chain_24_uneven()
     sysa = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=DEV),
