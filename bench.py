@@ -38,9 +38,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "iFCI increments/s & sigma TFLOP/s, 1 GB300, batched+mixed vs plain FP64 @1µEh"
 # dram__bytes_read.sum + dram__bytes_write.sum of one oz_contract_kernel launch
-# on CAS(6e,18o) (45.8 + 850.3 MB, 171 x 665,856 G elements); set to None
-# whenever that kernel changes until it is captured again
-OZ_DRAM_BYTES_PER_G_ELEMENT = (45.8e6 + 850.3e6) / (171 * 665856)
+# on CAS(6e,18o) (45.65 + 850.18 MB, 171 x 665,856 G elements; ncu capture of
+# `bench.py --case sigma --precision fp64e`); set to None whenever that kernel
+# changes until it is captured again
+OZ_DRAM_BYTES_PER_G_ELEMENT = (45.652992e6 + 850.175232e6) / (171 * 665856)
 UNIT = "increments/s"
 
 
@@ -654,8 +655,9 @@ def c2_case(args, torch, ifci):
     dev = torch.device("cuda", 0)
     chain = chain_7x2()
     X = tuple(range(7))
-    runs = [("fp64", "fp64", "fp64"), ("fp32+fp64", "fp32", "fp64"), ("bf16+fp64", "bf16", "fp64"),
-            ("bf16+fp64e", "bf16", "fp64e"), ("fp64e", "fp64e", "fp64e")]
+    runs = [("fp64", "fp64", "fp64"), ("fp32+fp64", "fp32", "fp64"), ("tf32+fp64", "tf32", "fp64"),
+            ("bf16+fp64", "bf16", "fp64"), ("tf32+fp64e", "tf32", "fp64e"), ("bf16+fp64e", "bf16", "fp64e"),
+            ("fp64e", "fp64e", "fp64e")]
     res = {}
     with ifci.Handle(0, 0) as h:
         sysd = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=dev),

@@ -46,7 +46,7 @@ namespace ifci {
 
 constexpr int kPairBits = 9;       // pair index < 512  => norb <= 31
 constexpr int kBlk16 = 16;         // 16-pair blocks of the tensor-core paths (npair <= 256)
-constexpr int kBlk16Stride = 20;   // bytes per string in the block-offset table
+constexpr int kBlk16Stride = 20;   // bytes per string in the block-offset table (19 blocks: npair <= 304)
 constexpr int kMaxNorb = 31;
 constexpr int kMaxStr = 1 << 22;
 
@@ -87,7 +87,8 @@ int set_error(ifci_handle_t h, int code, const char *fmt, ...);
     } while (0)
 
 // profiling ---------------------------------------------------------------
-enum ProfKind { PK_GATHER = 0, PK_CONTRACT = 1, PK_SCATTER = 2, PK_VECTOR = 3, PK_OTHER = 4, PK_CONTRACT_HI = 5 };
+enum ProfKind { PK_GATHER = 0, PK_CONTRACT = 1, PK_SCATTER = 2, PK_VECTOR = 3, PK_OTHER = 4, PK_CONTRACT_HI = 5,
+                PK_SETUP = 6 };
 void prof_begin(ifci_handle_t h, cudaStream_t s, int kind);
 void prof_end(ifci_handle_t h, cudaStream_t s);
 void prof_collect(ifci_handle_t h);   // adds finished event pairs to the totals (synchronises them)

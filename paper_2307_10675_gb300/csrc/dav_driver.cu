@@ -411,17 +411,20 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
         IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.pact[u], pact[u].data(), pact[u].size(), cudaMemcpyHostToDevice, s));
         IFCI_TRY(launch_compact_pair_map(h, nstr, np, mem.pm[k], (int)act[u].size(), mem.act[u], mem.pmapc[u], s));
     }
-    int maxnp = 0;
-    for (const Unit &U : units) maxnp = std::max(maxnp, U.spec.n * (U.spec.n + 1) / 2);
-    IFCI_TRY(launch_fold(h, nu, mem.fold, maxnp, s));
-    if (lo) IFCI_TRY(launch_convert_w(h, nu, lop.d_probs, s));
-    if (tc) IFCI_TRY(launch_tc_pack_w(h, nu, lop.d_probs, o.precision, s));
-    if (oz) IFCI_TRY(launch_oz_pack_w(h, nu, hi.d_probs, s));
-    IFCI_TRY(launch_hdiag(h, mem.hdu, mem.hwp, mem.hws, (int)hw_prob.size(), kVecChunk, s));
-    if (b.any_sector) IFCI_TRY(launch_sector_hd(h, b, s));
-    b.d_pidx = mem.pidx;
-    b.d_pcount = mem.pcount;
-    IFCI_TRY(dav_init(h, b, mem.hdp, s));
+    {
+        ProfScope ps(h, s, PK_SETUP);
+        int maxnp = 0;
+        for (const Unit &U : units) maxnp = std::max(maxnp, U.spec.n * (U.spec.n + 1) / 2);
+        IFCI_TRY(launch_fold(h, nu, mem.fold, maxnp, s));
+        if (lo) IFCI_TRY(launch_convert_w(h, nu, lop.d_probs, s));
+        if (tc) IFCI_TRY(launch_tc_pack_w(h, nu, lop.d_probs, o.precision, s));
+        if (oz) IFCI_TRY(launch_oz_pack_w(h, nu, hi.d_probs, s));
+        IFCI_TRY(launch_hdiag(h, mem.hdu, mem.hwp, mem.hws, (int)hw_prob.size(), kVecChunk, s));
+        if (b.any_sector) IFCI_TRY(launch_sector_hd(h, b, s));
+        b.d_pidx = mem.pidx;
+        b.d_pcount = mem.pcount;
+        IFCI_TRY(dav_init(h, b, mem.hdp, s));
+    }
 
     int *h_nactive = nullptr;
     IFCI_CUDA_TRY(h, cudaMallocHost(&h_nactive, 2 * sizeof(int)));

@@ -66,7 +66,7 @@ __global__ void build_strings_kernel(int n, int m, int nstr, int nexc, Binom B,
 }
 
 // blk[I][b] = index of the first entry of string I's excitation list whose
-// pair is >= 16 b, for b = 0 .. kBlk16 (lists are sorted by pair, so the
+// pair is >= 16 b, for b = 0 .. kBlk16Stride - 1 (lists are sorted by pair, so the
 // entries of the 16-pair block b are [blk[I][b], blk[I][b + 1])).
 __global__ void exc_blocks_kernel(int nstr, int nexc, const int32_t *__restrict__ exc, uint8_t *__restrict__ blk) {
     int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -74,7 +74,7 @@ __global__ void exc_blocks_kernel(int nstr, int nexc, const int32_t *__restrict_
     const int32_t *row = exc + (size_t)I * nexc;
     uint8_t *out = blk + (size_t)I * kBlk16Stride;
     int e = 0;
-    for (int b = 0; b <= kBlk16; b++) {
+    for (int b = 0; b < kBlk16Stride; b++) {   // 19 blocks + the end: npair up to 304
         while (e < nexc && exc_pair(row[e]) < 16 * b) e++;
         out[b] = (uint8_t)e;
     }
