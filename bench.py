@@ -528,7 +528,7 @@ def main():
 
 
 def paths_sample(ifci, torch, handle, chain, sysd, args, dev):
-    """FP64E, plain FP64 and mixed BF16 (+FP64E restarts) on the same seeded
+    """FP64E, plain FP64 and mixed BF16 and TF32 (+FP64E restarts) on the same seeded
     sample of body sets (their frozen-body CI problems through
     ifci_davidson_batched, one batch per path): increments/s of each path and
     the largest energy difference from the plain FP64 path."""
@@ -538,7 +538,8 @@ def paths_sample(ifci, torch, handle, chain, sysd, args, dev):
         h1, eri, ec = ifci.ifci_frozen_core(handle, sysd, X)
         probs.append(ifci.CIProblem(n, k, h1, eri, ec))
     res = {}
-    for name, prec, hi in (("fp64e", "fp64e", "fp64e"), ("fp64", "fp64", "fp64"), ("bf16_mixed", "bf16", "fp64e")):
+    for name, prec, hi in (("fp64e", "fp64e", "fp64e"), ("fp64", "fp64", "fp64"), ("bf16_mixed", "bf16", "fp64e"),
+                           ("tf32_mixed", "tf32", "fp64e")):
         o = ifci.davidson_opts(prec, hi_precision=hi, r_tol=R_TOL, e_tol=E_TOL, max_iter=300)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -701,7 +702,8 @@ def c4_case(args, torch, ifci):
     sysd = ifci.SystemArrays(chain.body_offsets, torch.tensor(chain.h, device=dev),
                              torch.tensor(chain.eri_packed(), device=dev))
     nsub = len(subset_sizes(chain, 3))
-    paths = [("fp64e", "fp64e", "fp64e"), ("bf16+fp64e", "bf16", "fp64e"), ("fp64", "fp64", "fp64")]
+    paths = [("fp64e", "fp64e", "fp64e"), ("bf16+fp64e", "bf16", "fp64e"), ("tf32+fp64e", "tf32", "fp64e"),
+             ("fp64", "fp64", "fp64")]
     res, ex = {}, {}
     with ifci.Handle(0, 0) as h:
         for name, prec, hi in paths:

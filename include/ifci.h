@@ -109,7 +109,8 @@ int ifci_wait_selftest(ifci_handle_t handle, long long limit_cycles, ifci_stream
  * Classes: 0 sigma gather (and quantisation), 1 sigma contraction (FP64,
  * FP32, BF16, TF32), 2 sigma scatter, 3 Davidson vector kernels, 4 other,
  * 5 FP64-emulating tensor-core contraction, 6 Davidson set-up (integral
- * folds and images, diagonals, P-space start).  ifci_profile_read synchronises the
+ * folds and images, diagonals, start vectors), 7 P-space eigensolves of the
+ * start.  ifci_profile_read synchronises the
  * recorded events and returns the accumulated milliseconds and launches. */
 int ifci_profile_enable(ifci_handle_t handle, int enable);
 int ifci_profile_read(ifci_handle_t handle, int kind, double *ms, long long *launches);

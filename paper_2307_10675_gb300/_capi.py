@@ -32,7 +32,7 @@ EXPORTS = [
     "ifci_sigma_noalloc", "ifci_sigma_noalloc_max_bytes", "ifci_h_elements", "ifci_wait_selftest",
     "ifci_hbci_batched",
 ]
-PROFILE_KINDS = {"gather": 0, "contract": 1, "scatter": 2, "vector": 3, "other": 4, "contract_hi": 5, "setup": 6}
+PROFILE_KINDS = {"gather": 0, "contract": 1, "scatter": 2, "vector": 3, "other": 4, "contract_hi": 5, "setup": 6, "pspace": 7}
 
 
 class Strings(ctypes.Structure):

@@ -88,7 +88,7 @@ int set_error(ifci_handle_t h, int code, const char *fmt, ...);
 
 // profiling ---------------------------------------------------------------
 enum ProfKind { PK_GATHER = 0, PK_CONTRACT = 1, PK_SCATTER = 2, PK_VECTOR = 3, PK_OTHER = 4, PK_CONTRACT_HI = 5,
-                PK_SETUP = 6 };
+                PK_SETUP = 6, PK_PSPACE = 7 };
 void prof_begin(ifci_handle_t h, cudaStream_t s, int kind);
 void prof_end(ifci_handle_t h, cudaStream_t s);
 void prof_collect(ifci_handle_t h);   // adds finished event pairs to the totals (synchronises them)

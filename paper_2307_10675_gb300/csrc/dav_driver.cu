@@ -149,6 +149,13 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
                 }
         hi.probs[u].npc = (int)act[u].size();
     }
+    std::vector<size_t> act_off(nu + 1, 0), pact_off(nu + 1, 0);
+    int ncompact = 0;
+    for (int u = 0; u < nu; u++) {
+        act_off[u + 1] = act_off[u] + act[u].size();
+        pact_off[u + 1] = pact_off[u] + pact[u].size();
+        if (!act[u].empty()) ncompact++;
+    }
     long long budget = o.det_budget > 0 ? o.det_budget : (1ll << 31);   // two 16 GB intermediates
     budget = std::max(budget, max_pd);
     budget = std::min(budget, std::max(sum_pd, max_pd));
@@ -170,6 +177,9 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
         std::vector<double *> hd, B, S, cblk;
         std::vector<int32_t *> act, pmapc;
         std::vector<uint8_t *> pact;
+        int32_t *act_all = nullptr;
+        uint8_t *pact_all = nullptr;
+        CompactDesc *cdesc = nullptr;
         int *sidx = nullptr;
         DavProb *probs = nullptr;
         DavState *state = nullptr;
@@ -202,12 +212,19 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
             // the alpha-only gathers where the pair map's offsets fit in int32
             if ((tc || oz) && 2ll * nstr * nstr < (1ll << 31)) m.pm[k] = c.take<int32_t>((size_t)nstr * pmap_ld(np));
         }
+        // active pairs of every sectored unit in one array each (one copy, one
+        // compaction launch for all units)
         m.act.assign(nu, nullptr); m.pmapc.assign(nu, nullptr); m.pact.assign(nu, nullptr);
+        m.act_all = c.take<int32_t>(act_off.back());
+        m.pact_all = c.take<uint8_t>(pact_off.back());
+        m.cdesc = c.take<CompactDesc>(ncompact);
         for (int u = 0; u < nu; u++) {
             if (act[u].empty()) continue;
             const int nstr = (int)binom(units[u].spec.n, units[u].spec.m);
-            m.act[u] = c.take<int32_t>(act[u].size());
-            m.pact[u] = c.take<uint8_t>(pact[u].size());
+            if (!c.count) {
+                m.act[u] = m.act_all + act_off[u];
+                m.pact[u] = m.pact_all + pact_off[u];
+            }
             m.pmapc[u] = c.take<int32_t>((size_t)nstr * pmap_ld((int)act[u].size()));
         }
         m.W.resize(nu); m.Wf.assign(nu, nullptr); m.Wtc.assign(nu, nullptr); m.Woz.assign(nu, nullptr);
@@ -403,13 +420,23 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
                                      cudaMemcpyHostToDevice, s));
     IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_gs, 0, (size_t)n * kMaxSpace * kMaxSpace * 8, s));
     IFCI_CUDA_TRY(h, cudaMemsetAsync(b.d_y, 0, (size_t)n * kYStride * 8, s));
-    for (int u = 0; u < nu; u++) {
-        if (!mem.act[u]) continue;
-        const int k = cls[{units[u].spec.n, units[u].spec.m}];
-        const int nstr = (int)binom(units[u].spec.n, units[u].spec.m), np = units[u].spec.n * (units[u].spec.n + 1) / 2;
-        IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.act[u], act[u].data(), act[u].size() * 4, cudaMemcpyHostToDevice, s));
-        IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.pact[u], pact[u].data(), pact[u].size(), cudaMemcpyHostToDevice, s));
-        IFCI_TRY(launch_compact_pair_map(h, nstr, np, mem.pm[k], (int)act[u].size(), mem.act[u], mem.pmapc[u], s));
+    if (ncompact > 0) {
+        std::vector<int32_t> act_h(act_off.back());
+        std::vector<uint8_t> pact_h(pact_off.back());
+        std::vector<CompactDesc> cd;
+        for (int u = 0; u < nu; u++) {
+            if (!mem.act[u]) continue;
+            std::copy(act[u].begin(), act[u].end(), act_h.begin() + act_off[u]);
+            std::copy(pact[u].begin(), pact[u].end(), pact_h.begin() + pact_off[u]);
+            const int k = cls[{units[u].spec.n, units[u].spec.m}];
+            const int nstr = (int)binom(units[u].spec.n, units[u].spec.m), np = units[u].spec.n * (units[u].spec.n + 1) / 2;
+            cd.push_back(CompactDesc{nstr, pmap_ld(np), (int)act[u].size(), pmap_ld((int)act[u].size()), mem.pm[k],
+                                     mem.act[u], mem.pmapc[u]});
+        }
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.act_all, act_h.data(), act_h.size() * 4, cudaMemcpyHostToDevice, s));
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.pact_all, pact_h.data(), pact_h.size(), cudaMemcpyHostToDevice, s));
+        IFCI_CUDA_TRY(h, cudaMemcpyAsync(mem.cdesc, cd.data(), cd.size() * sizeof(CompactDesc), cudaMemcpyHostToDevice, s));
+        IFCI_TRY(launch_compact_pair_maps(h, (int)cd.size(), mem.cdesc, s));
     }
     {
         ProfScope ps(h, s, PK_SETUP);
@@ -423,8 +450,8 @@ int dav_run(ifci_handle_t h, std::vector<Unit> &units, const std::vector<BlockSp
         if (b.any_sector) IFCI_TRY(launch_sector_hd(h, b, s));
         b.d_pidx = mem.pidx;
         b.d_pcount = mem.pcount;
-        IFCI_TRY(dav_init(h, b, mem.hdp, s));
     }
+    IFCI_TRY(dav_init(h, b, mem.hdp, s));
 
     int *h_nactive = nullptr;
     IFCI_CUDA_TRY(h, cudaMallocHost(&h_nactive, 2 * sizeof(int)));

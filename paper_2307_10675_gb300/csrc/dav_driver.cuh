@@ -68,8 +68,13 @@ int launch_sector_hd(ifci_handle_t h, const DavBatch &b, cudaStream_t s);
 int launch_unit_flags(ifci_handle_t h, const DavBatch &b, const int *hi, const int *lo, cudaStream_t s);
 int launch_sector_expand(ifci_handle_t h, const DavBatch &b, double *const *d_dst, cudaStream_t s);
 void orbital_groups(const uint32_t *adj, int n, std::vector<int> &label, int &ngroup);
-// pmapc[I][k] = pmap[I][act[k]] for the npc active pairs (rows of pmap_ld(npc), padded with -1)
-int launch_compact_pair_map(ifci_handle_t h, int nstr, int np, const int32_t *pmap, int npc, const int32_t *act,
-                            int32_t *pmapc, cudaStream_t s);
+// per unit: pmapc[I][k] = pmap[I][act[k]] for its npc active pairs (rows of
+// pmap_ld(npc), padded with -1); one block per unit, grid-stride
+struct CompactDesc {
+    int nstr, ld, npc, ldc;
+    const int32_t *pmap, *act;
+    int32_t *pmapc;
+};
+int launch_compact_pair_maps(ifci_handle_t h, int n, const CompactDesc *d_desc, cudaStream_t s);
 
 }  // namespace ifci

@@ -31,6 +31,7 @@
 
 #include "dav_driver.cuh"
 #include "hamiltonian.cuh"
+#include "slater.cuh"
 
 namespace ifci {
 
@@ -276,9 +277,8 @@ __device__ void jacobi_warp(double *A, double *V, int k, int lane) {
                     __syncwarp();
                     continue;
                 }
-                const double tau = (aqq - app) / (2.0 * apq);
-                const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+                double c, sn;
+                jacobi_rotation(app, aqq, apq, c, sn);
                 if (lane < k) {
                     const double arp = A[lane * kSolveLd + pp], arq = A[lane * kSolveLd + q];
                     A[lane * kSolveLd + pp] = c * arp - sn * arq;
@@ -850,11 +850,15 @@ __global__ void __launch_bounds__(256) mask_sigma_kernel(const DavProb *__restri
 
 int dav_init(ifci_handle_t h, DavBatch &b, const HdiagDesc *d_hd, cudaStream_t s) {
     const int nvi = (int)b.vitems.size();
-    init_kernel<<<stride_grid(h->device, b.nprob, 8), 256, 0, s>>>(b.d_probs, b.d_state, b.max_space, b.nprob);
-    IFCI_LAUNCH_CHECK(h);
-    init_vec_kernel<<<stride_grid(h->device, nvi, 8), 256, 0, s>>>(b.d_probs, b.d_vitems, b.max_space, nvi);
-    IFCI_LAUNCH_CHECK(h);
-    IFCI_TRY(launch_pspace_start(h, b, d_hd, s));
+    {
+        ProfScope ps(h, s, PK_SETUP);
+        init_kernel<<<stride_grid(h->device, b.nprob, 8), 256, 0, s>>>(b.d_probs, b.d_state, b.max_space, b.nprob);
+        IFCI_LAUNCH_CHECK(h);
+        init_vec_kernel<<<stride_grid(h->device, nvi, 8), 256, 0, s>>>(b.d_probs, b.d_vitems, b.max_space, nvi);
+        IFCI_LAUNCH_CHECK(h);
+    }
+    IFCI_TRY(launch_pspace_start(h, b, d_hd, s));   // its solve is profiled as PK_PSPACE
+    ProfScope ps(h, s, PK_SETUP);
     init_scale_kernel<<<stride_grid(h->device, nvi, 8), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part, nvi);
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;

@@ -209,9 +209,8 @@ __device__ __forceinline__ void psp_solve_kernel_body(const DavProb *__restrict_
                     __syncthreads();
                     continue;
                 }
-                const double tau = (aqq - app) / (2.0 * apq);
-                const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                const double c = 1.0 / sqrt(1.0 + tt * tt), sn = tt * c;
+                double c, sn;
+                jacobi_rotation(app, aqq, apq, c, sn);
                 __syncthreads();   // every thread has read A[pp][q], A[pp][pp], A[q][q]
                 if (t < P) {
                     const double arp = A[t * kPsp + pp], arq = A[t * kPsp + q];
@@ -391,14 +390,22 @@ int launch_pspace_start(ifci_handle_t h, const DavBatch &b, const HdiagDesc *d_h
     long long *pidx = b.d_pidx;
     int *pcount = b.d_pcount;
     if (!pidx || !pcount) return set_error(h, IFCI_ERR_OOM, "davidson: workspace (P-space)");
-    psp_select_kernel<<<stride_grid(h->device, b.nprob, 8), kSelThreads, 0, s>>>(b.d_probs, pidx, pcount, b.nprob);
-    IFCI_LAUNCH_CHECK(h);
+    {
+        ProfScope ps(h, s, PK_SETUP);
+        psp_select_kernel<<<stride_grid(h->device, b.nprob, 8), kSelThreads, 0, s>>>(b.d_probs, pidx, pcount, b.nprob);
+        IFCI_LAUNCH_CHECK(h);
+    }
     const int smem = 2 * kPsp * kPsp * (int)sizeof(double);   // 64 KB
     static SmemOptIn opt;
     IFCI_CUDA_TRY(h, ensure_smem(opt, h->device, psp_solve_kernel, smem));
-    psp_solve_kernel<<<stride_grid(h->device, b.nprob, 3), kPsp, smem, s>>>(b.d_probs, d_hd, pidx, pcount, b.d_state, b.max_space,
-                                                  b.d_blk_energy, b.nprob);
-    IFCI_LAUNCH_CHECK(h);
+    {
+        ProfScope ps(h, s, PK_PSPACE);
+        psp_solve_kernel<<<stride_grid(h->device, b.nprob, 3), kPsp, smem, s>>>(b.d_probs, d_hd, pidx, pcount,
+                                                                                 b.d_state, b.max_space,
+                                                                                 b.d_blk_energy, b.nprob);
+        IFCI_LAUNCH_CHECK(h);
+    }
+    ProfScope ps(h, s, PK_SETUP);
     norm_part_kernel<<<stride_grid(h->device, (long long)b.vitems.size(), 8), 256, 0, s>>>(b.d_probs, b.d_state, b.d_vitems, b.d_part, (int)b.vitems.size());
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;

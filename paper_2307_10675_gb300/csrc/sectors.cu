@@ -209,23 +209,23 @@ __global__ void __launch_bounds__(256) sector_expand_kernel(const DavProb *__res
 }
 
 // pair map of a sectored unit restricted to its active pairs
-__global__ void compact_pmap_kernel(int nstr, int ld, const int32_t *__restrict__ pmap, int npc, int ldc,
-                                    const int32_t *__restrict__ act, int32_t *__restrict__ pmapc) {
-    const long long n = (long long)nstr * ldc;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        const long long r = t / ldc;
-        const int k = (int)(t % ldc);
-        pmapc[t] = k < npc ? pmap[r * ld + act[k]] : -1;
+__global__ void __launch_bounds__(256) compact_pmaps_kernel(const CompactDesc *__restrict__ desc, int n) {
+    for (int u = blockIdx.x; u < n; u += gridDim.x) {
+        const CompactDesc d = desc[u];
+        const long long tot = (long long)d.nstr * d.ldc;
+        for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+            const long long r = t / d.ldc;
+            const int k = (int)(t % d.ldc);
+            d.pmapc[t] = k < d.npc ? d.pmap[r * d.ld + d.act[k]] : -1;
+        }
     }
 }
 
 }  // namespace
 
-int launch_compact_pair_map(ifci_handle_t h, int nstr, int np, const int32_t *pmap, int npc, const int32_t *act,
-                            int32_t *pmapc, cudaStream_t s) {
-    const long long n = (long long)nstr * pmap_ld(npc);
-    compact_pmap_kernel<<<stride_grid(h->device, (n + 255) / 256, 8), 256, 0, s>>>(nstr, pmap_ld(np), pmap, npc,
-                                                                                  pmap_ld(npc), act, pmapc);
+int launch_compact_pair_maps(ifci_handle_t h, int n, const CompactDesc *d_desc, cudaStream_t s) {
+    if (n <= 0) return IFCI_OK;
+    compact_pmaps_kernel<<<stride_grid(h->device, n, 8), 256, 0, s>>>(d_desc, n);
     IFCI_LAUNCH_CHECK(h);
     return IFCI_OK;
 }

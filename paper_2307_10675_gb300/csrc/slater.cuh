@@ -10,6 +10,35 @@
 
 namespace ifci {
 
+// Jacobi rotation (c, s) that zeroes A_pq of a symmetric matrix.  The angle
+// is taken in FP32 (its FP64 divides and square roots would cost ~40 FP64
+// operations, on a part whose FP64 rate is a small fraction of its FP32
+// rate), then (c, s) is scaled to c^2 + s^2 = 1 to FP64 rounding by two
+// Newton steps on 1 / sqrt(c^2 + s^2), so the rotation stays orthogonal and
+// the eigenvalues exact; the ~1e-7 error of the angle leaves A_pq at ~1e-7
+// of its size, which the next sweep removes.
+__device__ __forceinline__ void jacobi_rotation(double app, double aqq, double apq, double &c, double &s) {
+    if (fabs(apq) < 1e-30) {   // below FP32's normal range: FP64 throughout
+        const double tau = (aqq - app) / (2.0 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        c = 1.0 / sqrt(1.0 + t * t);
+        s = t * c;
+        return;
+    }
+    const float tau = (float)(aqq - app) / (2.0f * (float)apq);
+    const float tf = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+    const float cf = rsqrtf(1.0f + tf * tf);
+    double cc = cf, ss = (double)tf * (double)cf;
+#pragma unroll
+    for (int it = 0; it < 2; it++) {
+        const double k = 1.5 - 0.5 * (cc * cc + ss * ss);
+        cc *= k;
+        ss *= k;
+    }
+    c = cc;
+    s = ss;
+}
+
 __device__ __forceinline__ int between_parity(uint32_t m, int p, int q) {
     const int lo = min(p, q), hi = max(p, q);
     const uint32_t mask = ((1u << hi) - 1u) & ~((2u << lo) - 1u);
