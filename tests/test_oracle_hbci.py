@@ -123,3 +123,33 @@ def test_variational_bound_and_pt2_at_paper_thresholds(X):
     res = hbci.hbci_subsystem(s, X, eps1=1e-3, eps2=1e-6)
     if res.e_var - exact > 1e-8:
         assert abs(res.e_total - exact) < abs(res.e_var - exact)
+
+
+def test_charge_transfer_ground_state_outside_the_selection():
+    """The 24-body chain's set (15, 17): its lowest singlet (FCI) lies 0.41 Eh
+    below the lowest state reachable from the reference through contributions
+    above 1 mHa, so HBCI at the paper's thresholds stays there; eps1 = 0
+    selects every determinant and reaches FCI.  A property of the method that
+    the GPU path must share (it is compared set by set with this oracle)."""
+    from synth import chain_24_uneven
+    c = chain_24_uneven()
+    X = (15, 17)
+    exact = fci.solve_subsystem(c, X, method="dense").energy
+    paper = hbci.hbci_subsystem(c, X, 1e-3, 1e-6)
+    full = hbci.hbci_subsystem(c, X, 0.0, 0.0)
+    assert paper.e_total - exact > 0.4
+    assert paper.nsel < full.nsel == 2025
+    assert full.e_var == pytest.approx(exact, abs=1e-10)
+
+
+def test_reference_determinant_index_matches_the_oracle():
+    """The package's host helper for HBCI start determinants (rank of the
+    string of bonding orbitals) against the oracle's own reference index."""
+    import paper_2307_10675_gb300 as ifci
+    from synth import chain_24_uneven
+    c = chain_24_uneven()
+    for X in [(0,), (0, 1), (5, 7), (8, 11, 12), (2, 9, 16), (1, 3, 5, 7)]:
+        sub = fci.subsystem(c, X)
+        H = fci.Hamiltonian(sub)
+        bonding_local = [sub.ncore + sub.active.index(c.bonding_orbital(b)) for b in X]
+        assert ifci.reference_determinant(c.body_sizes, X) == H.reference_index(bonding_local), X
