@@ -370,7 +370,8 @@ int ifci_num_subsets(int nbody, int max_order, long long *count);
 
 /* ifci_increments — the iFCI expansion truncated at max_order (Eqs. 1-5).
  *   e0      : host double*, reference energy E_0.
- *   e_x     : host double[nsub] or NULL, E_X per body set (NaN if screened).
+ *   e_x     : host double[nsub] or NULL, E_X per body set (NaN if screened;
+ *             E_var + E_PT2 with opts->hbci_max_rounds > 0).
  *   eps     : host double[nsub], increments eps_X.
  *   e_total : host double*, E_0 + sum eps_X.
  *   iters   : host int[nsub] or NULL, sigma builds per set (HBCI: variational steps).
