@@ -132,3 +132,28 @@ def test_increments_with_hbci_match_the_oracle_expansion(handle):
     assert out["e_total"] == pytest.approx(total, abs=1e-8)
     with pytest.raises(ifci.IfciError):
         ifci.ifci_rdm_backward(handle, sysd, 4, 1.0, ifci.davidson_opts("fp64e", hbci_max_rounds=50))
+
+
+def test_hbci_batch_matches_stored_oracle_energies(handle):
+    """24 seeded 2-body sets of the 24-body chain in one batched call against
+    the oracle's stored HBCI results at the paper's thresholds
+    (tests/golden/chain24_hbci_oracle.json, written by
+    make_chain24_hbci_golden.py; every selection decision there lies at least
+    1e-6 Eh from eps1)."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "chain24_hbci_oracle.json")))
+    chain = chain_24_uneven()
+    keys = [k for k, g in gold["sets"].items() if g["margin1"] >= 2e-7]
+    sets = [tuple(int(v) for v in k.split(",")) for k in keys]
+    assert len(sets) >= 20
+    out = ifci.ifci_hbci_batched(handle, _problems(handle, chain, sets),
+                                 [ifci.reference_determinant(chain.body_sizes, X) for X in sets],
+                                 eps1=gold["eps1"], eps2=gold["eps2"],
+                                 opts=ifci.davidson_opts("fp64e", r_tol=1e-8, e_tol=1e-12, max_iter=300))
+    assert np.all(out["status"] == 0)
+    for i, k in enumerate(keys):
+        g = gold["sets"][k]
+        assert out["nsel"][i] == g["nsel"] and out["rounds"][i] == g["rounds"], k
+        assert out["e_var"][i] == pytest.approx(g["e_var"], abs=1e-8), k
+        assert out["e_pt2"][i] == pytest.approx(g["e_pt2"], abs=1e-9), k
