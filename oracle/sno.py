@@ -142,3 +142,13 @@ def sno_energy(system, X: Sequence[int], eta: float, h: np.ndarray = None, eri: 
     H = fci.Hamiltonian(sub)
     e, _ = fci.lowest_singlet_dense(H)
     return e, Tv.shape[1]
+
+
+def sno_energies(system, max_order: int, eta: float):
+    """(E_0, {X: E_X}, {X: eps_X}, E_total) of the expansion with every E_X in
+    the SNO space of X (Eqs. 1-5 unchanged; E_c(X) = E_X - E_0)."""
+    eri = _eri_full(system)
+    e0 = fci.reference_energy(system)
+    ex = {X: sno_energy(system, X, eta, system.h, eri)[0] for X in fci.body_subsets(system.nbody, max_order)}
+    eps = fci.increments_from_correlation({X: e - e0 for X, e in ex.items()})
+    return e0, ex, eps, e0 + sum(eps.values())

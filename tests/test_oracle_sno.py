@@ -95,3 +95,17 @@ def test_rotation_of_the_virtuals_changes_nothing():
         e2, n2 = sno.sno_energy(s, X, 4.0, h2, eri2)
         assert n1 == n2
         assert e1 == pytest.approx(e2, abs=1e-9)
+
+
+def test_full_order_sno_expansion_keeping_everything_is_fci():
+    """At full order the expansion telescopes to E of the set of all bodies;
+    keeping every natural orbital that set's space is every orbital: the
+    total equals FCI(8e,8o) of the 4 x 2 chain (Slater–Condon, dense)."""
+    s = chain_4x2()
+    _, _, _, total = sno.sno_energies(s, 4, eta=300.0)
+    h, eri = _loc_integrals(s, list(range(s.norb)))
+    e_fci, _ = fci.lowest_singlet_dense(fci.Hamiltonian(fci.Subsystem([], list(range(s.norb)), 4, h, eri)))
+    assert total == pytest.approx(e_fci, abs=1e-9)
+    # a truncated space at full order is variational
+    _, _, _, total_cut = sno.sno_energies(s, 4, eta=2.0)
+    assert total_cut >= e_fci - 1e-10
